@@ -1,0 +1,179 @@
+/*
+ * hweno.h -- C ABI of libhweno, the B300 (sm_103a) implementation of the
+ * per-cell, per-stage spatial operator of the fifth-order finite-volume
+ * derivative-based HWENO scheme with unified stencils (arxiv 2607.24325).
+ *
+ * Problem (Sec. 1, Eq. hyperbolic-conservation-laws): u_t + div F(u) = 0,
+ * u(x, 0) = u0(x), in 1D (Sec. 2.1) or 2D (Sec. 2.2) on a uniform grid, with
+ * F = advection, Burgers or the Euler equations of gas dynamics (Examples
+ * 2, 4-9).  The library evolves the cell averages u-bar together with the
+ * derivative moments v-bar (and w-bar in 2D), reconstructs from the unified
+ * compact stencils without the target cell's own derivatives (Step 1-3),
+ * applies global Lax-Friedrichs fluxes and the SSP-RK3 update with the
+ * limited derivatives substituted at every stage (Step 4), characteristic-wise
+ * for Euler (Remark 1).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns hweno_status; nothing throws or aborts across the ABI.
+ *    On failure hweno_last_error() (thread-local) describes the cause.
+ *  - Arrays are SoA planes, x fastest, no ghost cells: U[f][j][i] with
+ *    f = d*nc + k, d = 0 cell averages, 1 x-derivative moments, 2
+ *    y-derivative moments (2D); k the conserved component (nc = 1 for scalar
+ *    equations, 3 for 1D Euler (rho, rho u, E), 4 for 2D Euler
+ *    (rho, rho u, rho v, E)).  1D v-bar is the mean of u_x over the cell
+ *    (Sec. 2.1); 2D v-bar = (1/dy) int u_x dOmega and w-bar = (1/dx) int u_y
+ *    dOmega are the scaled moments of Sec. 2.2.
+ *  - Element type is double for HWENO_FP64 solvers and float for HWENO_FP32.
+ *  - Pointers flagged on_device are device pointers on the current device;
+ *    otherwise host pointers (pinned or pageable).  The caller owns every
+ *    buffer it passes; the library owns its internal workspace (stage states,
+ *    the stage-1 limited derivatives, the device control block).
+ *  - Work runs on the solver's own CUDA stream (hweno_stream()).  A call that
+ *    takes caller device buffers first waits for the caller's stream given
+ *    at creation and, before returning, makes that stream wait for the
+ *    library's work, so stream-ordered callers (e.g. PyTorch) need no extra
+ *    synchronisation.  Calls that return host data synchronise.
+ *  - Device-side faults and non-physical states (NaN, negative density or
+ *    pressure) surface as HWENO_ERR_CUDA / HWENO_ERR_NONPHYSICAL at the next
+ *    call that synchronises.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HWENO_OK = 0,
+  HWENO_ERR_ARG = 1,          /* invalid argument (reported, nothing changed) */
+  HWENO_ERR_CUDA = 2,         /* CUDA runtime error */
+  HWENO_ERR_NONPHYSICAL = 3,  /* NaN / Inf / non-positive density or pressure */
+  HWENO_ERR_TIMEOUT = 4,      /* a bounded device wait gave up */
+  HWENO_ERR_OOM = 5,          /* device allocation failed */
+  HWENO_ERR_STATE = 6         /* call out of order (e.g. no state set) */
+} hweno_status;
+
+enum { HWENO_EQ_ADVECTION = 0, HWENO_EQ_BURGERS = 1, HWENO_EQ_EULER = 2 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECT = 2, HWENO_BC_INFLOW = 3 };
+enum { HWENO_FP64 = 0, HWENO_FP32 = 1 };
+enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
+
+/* Problem statement and scheme parameters.
+ *  dim            1 or 2
+ *  nx, ny         cells per direction (>= 3; ny ignored in 1D)
+ *  xlo..yhi       domain [xlo, xhi] (x [ylo, yhi])
+ *  equation       HWENO_EQ_*; adv_x, adv_y the advection velocity;
+ *                 gamma_gas the ratio of specific heats (Euler)
+ *  lin_w          linear weights gamma_0..gamma_2 (1D) / gamma_0..gamma_4
+ *                 (2D), each > 0, summing to 1 (Eq. rewrite, rewrite-2D);
+ *                 the paper's experiments use 1/400 per linear polynomial
+ *  eps            epsilon of the nonlinear weights (paper: 1e-8)
+ *  weight_pow     power of beta in the weight denominator: 1 (beta + eps,
+ *                 which reproduces the paper's tables in 1D and 2D) or 2
+ *                 (beta^2 + eps, as printed in Eq. nonlinear-weights-2D)
+ *  charwise       Euler: 1 characteristic-wise (Remark 1), 0 component-wise
+ *  linear_weights 1: omega = gamma everywhere (the linear reconstruction p0)
+ *  cfl, dt_rule   dt = cfl h / alpha with h = dx (HWENO_DT_CFL) or dx^(5/3)
+ *                 (HWENO_DT_CFL_DX53, for order studies); 2D uses
+ *                 cfl / (alpha_x/hx + alpha_y/hy)
+ *  bc[4]          x-low, x-high, y-low, y-high: HWENO_BC_*
+ *  bc_state[4][4] conservative state imposed by HWENO_BC_INFLOW sides
+ *  precision      HWENO_FP64 or HWENO_FP32 (storage and stencil arithmetic)
+ */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double xlo, xhi, ylo, yhi;
+  int equation;
+  double adv_x, adv_y, gamma_gas;
+  double lin_w[5];
+  double eps;
+  int weight_pow;
+  int charwise;
+  int linear_weights;
+  double cfl;
+  int dt_rule;
+  int bc[4];
+  double bc_state[4][4];
+  int precision;
+} hweno_config;
+
+typedef struct hweno_solver hweno_solver;
+typedef struct hweno_batch hweno_batch;
+
+/* Thread-local description of the last failure of this thread (never NULL). */
+const char* hweno_last_error(void);
+/* Library version string. */
+const char* hweno_version(void);
+
+/* Create a solver for one grid (Sec. 2.1 / 2.2).  cuda_stream is the
+ * caller's cudaStream_t (NULL = legacy default stream) that data calls order
+ * against.  Allocates the library workspace on the current device.
+ * Errors: HWENO_ERR_ARG (bad config), HWENO_ERR_OOM, HWENO_ERR_CUDA. */
+hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_solver** out);
+/* Free the solver and its workspace (NULL is a no-op). */
+void hweno_destroy(hweno_solver* s);
+/* The solver's own CUDA stream (cudaStream_t), on which kernels run. */
+void* hweno_stream(hweno_solver* s);
+/* Number of stored fields nf = nc * (dim + 1) and cells per field. */
+hweno_status hweno_shape(const hweno_solver* s, int* nfields, size_t* ncells);
+
+/* Copy a state in (U[nf][ny][nx]) and compute its wave speeds; resets t. */
+hweno_status hweno_set_state(hweno_solver* s, const void* U, int on_device);
+/* Copy the current state out (same layout); synchronises if !on_device. */
+hweno_status hweno_get_state(hweno_solver* s, void* U, int on_device);
+
+/* Max spectral radius over the cell averages of the current state
+ * (alpha of the global Lax-Friedrichs flux, Sec. 2.1 and 2.2).  Synchronises. */
+hweno_status hweno_alpha(hweno_solver* s, double* alpha_x, double* alpha_y);
+
+/* One application of the spatial operator to the current state with the
+ * given Lax-Friedrichs constants: L_out[nf][cells] = (L^u, L^v, L^w) of Eq.
+ * semi-discrete-scheme / 2D-semi-discrete-scheme-uniform, dhat_out[nc*dim]
+ * [cells] = the limited derivatives v-hat (and w-hat) of Step 3.  Both are
+ * caller device buffers of the solver's element type. */
+hweno_status hweno_apply_operator(hweno_solver* s, double alpha_x, double alpha_y,
+                                  void* L_out, void* dhat_out);
+
+/* One SSP-RK3 step (Step 4) with the given dt and Lax-Friedrichs constants. */
+hweno_status hweno_step(hweno_solver* s, double dt, double alpha_x, double alpha_y);
+
+/* Advance to t_final with the device-resident CFL time step (alpha from the
+ * averages at the start of each step, last step clipped to t_final), at most
+ * max_steps steps.  Steps are replayed from a captured CUDA graph; the host
+ * polls the device control block once per graph replay.  Returns the time
+ * reached and the steps taken.  HWENO_ERR_NONPHYSICAL if a state became
+ * non-physical (the state is left at the failing step). */
+hweno_status hweno_advance(hweno_solver* s, double t_final, int max_steps, double* t_out,
+                           int* steps_out);
+
+/* ---- Batches of independent 1D problems of uneven sizes (one launch per
+ * stage for all instances, per-instance alpha, dt, time and done flag). ---- */
+/* cfgs[n] are 1D configs with the same equation, precision and weights. */
+hweno_status hweno_batch_create(int n, const hweno_config* cfgs, void* cuda_stream,
+                                hweno_batch** out);
+void hweno_batch_destroy(hweno_batch* b);
+void* hweno_batch_stream(hweno_batch* b);
+/* Total cells (sum of nx) and per-instance offsets (n+1 entries, host). */
+hweno_status hweno_batch_layout(const hweno_batch* b, size_t* total_cells, size_t* offsets);
+/* U is [nf][total_cells]: instance k owns cells offsets[k] .. offsets[k+1]-1
+ * of every field plane. */
+hweno_status hweno_batch_set_state(hweno_batch* b, const void* U, int on_device);
+hweno_status hweno_batch_get_state(hweno_batch* b, void* U, int on_device);
+/* Advance every instance k to t_final[k] (host array); at most max_steps
+ * steps per instance.  t_out, steps_out (host, may be NULL) receive per
+ * instance results. */
+hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_steps,
+                                 double* t_out, int* steps_out);
+/* Apply the operator to every instance with per-instance alpha (host array):
+ * L_out [nf][total], dhat_out [nc][total] (device buffers). */
+hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,
+                                        void* dhat_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
