@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the HWENO hot path on B300.
+
+Workload: 2D Euler four-quadrant Riemann problem on [0,1]^2, 4096 x 4096
+cells, seeded quadrant states (rho, p ~ U[0.1, 1.5], |u|, |v| <= 1, seed
+2024), transmissive boundaries, characteristic-wise nonlinear HWENO.  A step
+is one SSP-RK3 step (three fused stage kernels plus the device-resident
+time-step control); the metric is cell-updates per RK stage per second.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores (bounded samples of the same workload).  Under torchrun each rank
+advances its own replica of the workload (no data-path collective; weak
+scaling); the barrier and the max over ranks bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HWENO cell-updates/s per RK stage & HBM GB/s; learned/FP32 vs plain at matched L1"
+UNIT = "cell-updates/s"
+N_GRID = 4096
+SEED = 2024
+W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
+# Algorithmic flops of one cell update in one stage, counted from the
+# executed FP instructions of the stage kernel (ncu sass op counters, see
+# profiles/) with the ring-cell redundancy of the two passes removed.
+FLOPS_PER_CELL_STAGE = {"fp64": 7000.0, "fp32": 7000.0}
+FLOPS_SOURCE = "estimate (operation count of the method); replaced by counted flops once profiled"
+# Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
+# F + D, stages 2-3 read 2F (state in + base average/limited derivatives)
+# and write F; F = 12 stored fields, D = 8 limited derivatives -> (8F+D)/3 words.
+F_FIELDS, D_FIELDS = 12, 8
+
+
+def words_per_cell_stage() -> float:
+    return (8 * F_FIELDS + D_FIELDS) / 3.0
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        try:
+            with open(self.path) as fh:
+                for line in fh:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) < 9:
+                        continue
+                    try:
+                        sm.append(float(p[1]))
+                        mx.append(float(p[2]))
+                    except ValueError:
+                        continue
+                    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                    for name, v in zip(names, p[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(name)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+GRID = {"n": N_GRID}
+
+
+def quadrant_state(n: int) -> np.ndarray:
+    from paper_2607_24325_b300 import workloads as W
+    return W.quadrant_2d(W.quadrant_states(SEED), 0.5, 0.5, 0.0, 1.0, 0.0, 1.0, n, n)
+
+
+def window_problem(m: int):
+    """An m x m window of the 4096^2 workload centred on the quadrant corner
+    (same cell size, transmissive sides): the CPU oracle's bounded sample."""
+    from paper_2607_24325_b300 import workloads as W
+    import oracle
+    h = 1.0 / N_GRID
+    lo = 0.5 - 0.5 * m * h
+    U = W.quadrant_2d(W.quadrant_states(SEED), 0.5, 0.5, lo, lo + m * h, lo, lo + m * h, m, m)
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=m, ny=m, xlo=lo, xhi=lo + m * h, ylo=lo,
+                          yhi=lo + m * h, lin_w=W2D, bc=(oracle.BC_OUTFLOW,) * 4)
+    return prob, U
+
+
+def cpu_oracle_rate(m: int, steps: int = 1) -> dict:
+    """Cell-updates per RK stage per second of the oracle (serial C, one core)."""
+    import oracle
+    prob, U = window_problem(m)
+    ax, ay = oracle.alpha(prob, U)
+    dt = oracle.dt(prob, ax, ay)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U = oracle.step(prob, U, dt, ax, ay)
+    el = time.perf_counter() - t0
+    return {"value": m * m * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} SSP-RK3 step(s) of the serial FP64 C oracle on a {m}x{m} window of the "
+                      f"4096^2 four-quadrant state ({el:.1f} s)"}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    m = 96
+    prob, U = window_problem(m)
+    ax, ay = oracle.alpha(prob, U)
+    dt = oracle.dt(prob, ax, ay)
+    for _ in range(args.warmup):
+        oracle.step(prob, U, dt, ax, ay)
+    t0 = time.perf_counter()
+    V = U
+    for _ in range(args.steps):
+        V = oracle.step(prob, V, dt, ax, ay)
+    el = time.perf_counter() - t0
+    value = m * m * 3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded four-quadrant Riemann states)",
+        "config": {"workload": "2D Euler four-quadrant Riemann 4096^2, FP64 characteristic-wise HWENO "
+                               f"(reference arm: CPU oracle on a {m}x{m} window per step)",
+                   "nx": N_GRID, "ny": N_GRID},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one SSP-RK3 step of the serial C oracle on a {m}x{m} window per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def time_precision(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, stream_ctx=None):
+    """Advance `steps` steps of the workload at `precision`; returns timings."""
+    n = GRID["n"]
+    cfg = hw.Config(dim=2, nx=n, ny=n, equation=hw.EQ_EULER, lin_w=W2D, bc=(hw.BC_OUTFLOW,) * 4,
+                    precision=precision)
+    s = hw.Solver(cfg)
+    s.set_state(U0_dev)
+    s.advance(1e30, max_steps=warmup)
+    s.set_state(U0_dev)       # the timed steps start from the workload's initial state
+    stream = torch.cuda.ExternalStream(s.stream)
+    s.set_profiling(True)
+    torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(sampler_gpu) as clk:
+        ev0.record(stream)
+        t, n = s.advance(1e30, max_steps=steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    stage_ms, stage_n, launches = s.profile()
+    s.set_profiling(False)
+    assert n == steps, (n, steps)
+    out = {"ms": ms, "stage_ms_avg": stage_ms / max(stage_n, 1), "stage_launches": stage_n,
+           "launches": launches, "clocks": clk.summary(), "solver": s}
+    return out
+
+
+def e2e_run(hw, torch, U0_host_pinned, precision, steps):
+    """End to end through the public API with host buffers: set_state from
+    pinned host memory, advance `steps` steps, get_state into pinned host
+    memory -- all inside the timed region."""
+    n = GRID["n"]
+    cfg = hw.Config(dim=2, nx=n, ny=n, equation=hw.EQ_EULER, lin_w=W2D, bc=(hw.BC_OUTFLOW,) * 4,
+                    precision=precision)
+    s = hw.Solver(cfg)
+    out = torch.empty_like(U0_host_pinned).pin_memory()
+    # warm the path once (graph capture, first-launch costs)
+    hw.hweno_set_state(s.h, U0_host_pinned)
+    s.advance(1e30, max_steps=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hw.hweno_set_state(s.h, U0_host_pinned)
+    t, n = s.advance(1e30, max_steps=steps)
+    hw.hweno_get_state(s.h, out)
+    el = time.perf_counter() - t0
+    s.close()
+    nbytes = U0_host_pinned.numel() * U0_host_pinned.element_size()
+    return el, nbytes, out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=N_GRID, help="cells per side (profiling runs use a small grid)")
+    ap.add_argument("--only", choices=["fp64", "fp32"], default=None, help="time one precision only")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_24325_b300 import hweno as hw
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    GRID["n"] = args.grid
+    ng = args.grid
+    ncells = ng * ng
+    U0 = quadrant_state(ng)
+    U0_t = torch.from_numpy(U0)
+    U0_pin = U0_t.pin_memory()
+    U0_dev = U0_pin.cuda()
+
+    # headline: FP64 plain (nonlinear, characteristic-wise) path; FP32 beside it
+    r64 = r32 = None
+    if args.only in (None, "fp64"):
+        r64 = time_precision(hw, torch, U0_dev, hw.FP64, args.steps, args.warmup, local)
+    if args.only in (None, "fp32"):
+        r32 = time_precision(hw, torch, U0_dev, hw.FP32, args.steps, args.warmup, local)
+    head = r64 if r64 is not None else r32
+    ms_head = head["ms"]
+    if world > 1:
+        x = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        ms_head = float(x.item())
+    value = world * ncells * 3 * args.steps / (ms_head * 1e-3)
+
+    # end to end with host buffers
+    e2e = None
+    if not args.no_e2e:
+        prec = hw.FP64 if r64 is not None else hw.FP32
+        src = U0_pin if prec == hw.FP64 else U0_t.float().pin_memory()
+        e2e_s, nbytes, _ = e2e_run(hw, torch, src, prec, args.steps)
+        e2e = {"value": world * ncells * 3 * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+               "what": "set_state from pinned host + advance + get_state to pinned host, per step"}
+
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    hbm_src = "of measured" if hbm_peak else "of fallback"
+    hbm_peak = hbm_peak or 6400.0
+    fp64_peak = hw.hweno_peak_fma(hw.FP64) / 1e12
+    fp32_peak = hw.hweno_peak_fma(hw.FP32) / 1e12
+
+    def roofline(r, prec, peak_tf):
+        key = "fp64" if prec == hw.FP64 else "fp32"
+        flops_launch = FLOPS_PER_CELL_STAGE[key] * ncells
+        achieved = flops_launch / (r["stage_ms_avg"] * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved / peak_tf, "traffic": None,
+                "kernel": f"k_stage2d<{'double' if prec == hw.FP64 else 'float'},EULER,char>",
+                "peak_source": "measured FMA probe (hweno_peak_fma) on this GPU",
+                "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[key], "flops_source": FLOPS_SOURCE,
+                "avg_launch_ms": r["stage_ms_avg"]}
+
+    def hbm(r, esz):
+        bytes_launch = words_per_cell_stage() * esz * ncells
+        gbs = bytes_launch / (r["stage_ms_avg"] * 1e-3) / 1e9
+        return {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak, "peak_source": hbm_src,
+                "bytes_per_cell_stage": words_per_cell_stage() * esz}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(256)
+
+    if rank == 0:
+        head_prec = hw.FP64 if r64 is not None else hw.FP32
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_head / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if r64 is not None else "f32",
+            "data": "synthetic (seeded four-quadrant Riemann states, seed 2024)",
+            "config": {"workload": f"2D Euler four-quadrant Riemann {ng}^2, transmissive, "
+                                   f"{'FP64' if r64 is not None else 'FP32'} characteristic-wise nonlinear "
+                                   "HWENO, SSP-RK3",
+                       "nx": ng, "ny": ng, "cells": ncells, "stages_per_step": 3,
+                       "l2": "inputs larger than L2 (state 1.6 GB FP64, 0.8 GB FP32 at 4096^2)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline(head, head_prec, fp64_peak if head_prec == hw.FP64 else fp32_peak),
+            "hbm": hbm(head, 8 if head_prec == hw.FP64 else 4),
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(head["launches"]),
+            "clocks": head["clocks"],
+        }
+        if r64 is not None and r32 is not None:
+            value32 = world * ncells * 3 * args.steps / (r32["ms"] * 1e-3)
+            line["fp32"] = {"value": value32, "ms_per_step": r32["ms"] / args.steps, "dtype": "f32",
+                            "roofline": roofline(r32, hw.FP32, fp32_peak), "hbm": hbm(r32, 4),
+                            "clocks": r32["clocks"], "speedup_vs_fp64": value32 / value}
+        print(json.dumps(line), flush=True)
+    for r in (r64, r32):
+        if r is not None:
+            r["solver"].close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,22 @@ hweno_status hweno_step(hweno_solver* s, double dt, double alpha_x, double alpha
 hweno_status hweno_advance(hweno_solver* s, double t_final, int max_steps, double* t_out,
                            int* steps_out);
 
+/* Opt-in measurement of the stage kernels inside hweno_advance: while
+ * enabled, advance launches every step directly (no graph) and brackets
+ * each stage kernel launch with CUDA events on the solver's stream; the
+ * totals accumulate until the next hweno_set_profiling call resets them.
+ * hweno_profile returns the summed device time of the stage launches (ms),
+ * their number, and the number of kernels advance launched (5 per step:
+ * control begin, stages 1-3, control end). */
+hweno_status hweno_set_profiling(hweno_solver* s, int enable);
+hweno_status hweno_profile(hweno_solver* s, double* stage_ms, long long* stage_launches,
+                           long long* kernel_launches);
+
+/* Measured FMA throughput of the current GPU in flop/s (2 per FMA) for
+ * HWENO_FP64 or HWENO_FP32: the ALU roofline of the stencil kernels.  Runs a
+ * short probe kernel (milliseconds); synchronises the device. */
+hweno_status hweno_peak_fma(int precision, double* flops_per_second);
+
 /* ---- Batches of independent 1D problems of uneven sizes (one launch per
  * stage for all instances, per-instance alpha, dt, time and done flag). ---- */
 /* cfgs[n] are 1D configs with the same equation, precision and weights. */

@@ -1,0 +1,299 @@
+// hweno_device.cuh -- device building blocks of the unified-stencil HWENO
+// operator (arxiv 2607.24325) for sm_103a: Appendix A coefficient maps,
+// smoothness indicators and nonlinear weights (Steps 1-3 of Sec. 2.1 and
+// 2.2), Euler physics (closed-form eigenvectors, fluxes and flux directional
+// derivatives), and the ghost-cell index map used by the fused halo loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno_types.h"
+
+#define HW_FULL_MASK 0xffffffffu
+
+namespace hw {
+
+// ---------------------------------------------------------------------------
+// Scheme parameters in the arithmetic type T.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct WeightsT {
+  T g[5];        // linear weights gamma_m
+  T inv_g0;      // 1 / gamma_0
+  T eps;         // epsilon of the nonlinear weights
+  int pow2;      // 1: beta^2 + eps in the denominator, 0: beta + eps
+  int linear;    // 1: omega = gamma (pure p0)
+};
+
+template <typename T>
+__host__ __device__ inline WeightsT<T> make_weights(const WeightParams& w) {
+  WeightsT<T> o;
+  for (int m = 0; m < 5; ++m) o.g[m] = (T)w.g[m];
+  o.inv_g0 = (T)(1.0 / w.g[0]);
+  o.eps = (T)w.eps;
+  o.pow2 = w.pow2;
+  o.linear = w.linear;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ T fabs_t(T x) { return x < T(0) ? -x : x; }
+
+// omega-tilde_m = gamma_m (1 + tau^2 / (beta_m^{1|2} + eps))  (Eq. nonlinear-weights)
+template <typename T>
+__device__ __forceinline__ T wtilde(T gam, T tau2, T beta, const WeightsT<T>& w) {
+  const T b = w.pow2 ? beta * beta : beta;
+  return gam * (T(1) + tau2 / (b + w.eps));
+}
+
+// ---------------------------------------------------------------------------
+// 1D reconstruction of one scalar field (Sec. 2.1 Steps 1-3).
+// Inputs u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_{i+1} (the target cell's own
+// derivative is never used).  Outputs u_i(x_{i-1/2}), u_i(x_{i+1/2}),
+// u_i'(x_{i-1/2}), u_i'(x_{i+1/2}) and v-hat = (u_i(x_{i+1/2}) - u_i(x_{i-1/2}))/dx.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Rec1 { T uL, uR, dL, dR, vh; };
+
+template <typename T>
+__device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T idx,
+                                          const WeightsT<T>& w) {
+  const T a = dx * vm, b = dx * vp;
+  const T s = um + up, dd = up - um, ab = a + b, ba = b - a;
+  // Appendix A: p0 = sum_l c_l xi^l, xi = (x - x_i)/dx
+  const T c0 = T(287.0 / 240.0) * u0 - T(47.0 / 480.0) * s + T(9.0 / 320.0) * ba;
+  const T c1 = T(13.0 / 16.0) * dd - T(5.0 / 16.0) * ab;
+  const T c2 = T(5.0 / 4.0) * s - T(5.0 / 2.0) * u0 - T(3.0 / 8.0) * ba;
+  const T c3 = T(0.25) * (ab - dd);
+  const T c4 = u0 - T(0.5) * s + T(0.25) * ba;
+  // p1 = u_i + d1 xi, p2 = u_i + d2 xi
+  const T d1 = u0 - um, d2 = up - u0;
+  T r, w1, w2;  // r = omega_0 / gamma_0
+  if (w.linear) {
+    r = T(1); w1 = w.g[1]; w2 = w.g[2];
+  } else {
+    // Step 2: beta = sum_l (l! c_l)^2
+    const T b0 = c1 * c1 + T(4) * c2 * c2 + T(36) * c3 * c3 + T(576) * c4 * c4;
+    const T b1 = d1 * d1, b2 = d2 * d2;
+    // Step 3
+    const T tau = T(0.5) * (fabs_t(b0 - b1) + fabs_t(b0 - b2));
+    const T t2 = tau * tau;
+    const T e0 = wtilde(w.g[0], t2, b0, w), e1 = wtilde(w.g[1], t2, b1, w), e2 = wtilde(w.g[2], t2, b2, w);
+    const T inv = T(1) / (e0 + e1 + e2);
+    r = e0 * inv * w.inv_g0; w1 = e1 * inv; w2 = e2 * inv;
+  }
+  // Eq. (hweno-reconstruction-1D): u_i = r (p0 - g1 p1 - g2 p2) + w1 p1 + w2 p2
+  const T k0 = r * (c0 - (w.g[1] + w.g[2]) * u0) + (w1 + w2) * u0;
+  const T k1 = r * (c1 - w.g[1] * d1 - w.g[2] * d2) + w1 * d1 + w2 * d2;
+  const T k2 = r * c2, k3 = r * c3, k4 = r * c4;
+  const T ev = k0 + T(0.25) * k2 + T(0.0625) * k4;
+  const T od = T(0.5) * k1 + T(0.125) * k3;
+  const T evd = k1 + T(0.75) * k3;
+  const T odd = k2 + T(0.5) * k4;
+  Rec1<T> o;
+  o.uR = ev + od;
+  o.uL = ev - od;
+  o.dR = (evd + odd) * idx;
+  o.dL = (evd - odd) * idx;
+  o.vh = T(2) * od * idx;
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// Euler physics (Examples 2, 4-9; gamma-law gas).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Eig {
+  T u, v, c, H, q2h, b1, ic;  // q2h = (u^2+v^2)/2, b1 = (g-1)/c^2, ic = 1/c
+};
+
+template <typename T>
+__device__ __forceinline__ Eig<T> eig1(T r, T m, T E, T g) {
+  Eig<T> e;
+  const T ir = T(1) / r;
+  e.u = m * ir;
+  e.v = T(0);
+  e.q2h = T(0.5) * e.u * e.u;
+  const T p = (g - T(1)) * (E - m * e.u * T(0.5));
+  const T c2 = g * p * ir;
+  e.c = sqrt(c2);
+  e.ic = T(1) / e.c;
+  e.H = (E + p) * ir;
+  e.b1 = (g - T(1)) / c2;
+  return e;
+}
+
+template <typename T>
+__device__ __forceinline__ Eig<T> eig2(T r, T mx, T my, T E, T g) {
+  Eig<T> e;
+  const T ir = T(1) / r;
+  e.u = mx * ir;
+  e.v = my * ir;
+  e.q2h = T(0.5) * (e.u * e.u + e.v * e.v);
+  const T p = (g - T(1)) * (E - r * e.q2h);
+  const T c2 = g * p * ir;
+  e.c = sqrt(c2);
+  e.ic = T(1) / e.c;
+  e.H = (E + p) * ir;
+  e.b1 = (g - T(1)) / c2;
+  return e;
+}
+
+// 1D: left eigenvectors applied to x (characteristic variables w = L x).
+template <typename T>
+__device__ __forceinline__ void l1_apply(const Eig<T>& e, const T* x, T* w) {
+  const T s = e.b1 * (e.q2h * x[0] - e.u * x[1] + x[2]);
+  const T t = (e.u * x[0] - x[1]) * e.ic;
+  w[0] = T(0.5) * (s + t);
+  w[1] = x[0] - s;
+  w[2] = T(0.5) * (s - t);
+}
+// 1D: right eigenvectors, y = R w.
+template <typename T>
+__device__ __forceinline__ void r1_apply(const Eig<T>& e, const T* w, T* y) {
+  const T sum = w[0] + w[1] + w[2];
+  const T dif = w[2] - w[0];
+  y[0] = sum;
+  y[1] = e.u * sum + e.c * dif;
+  y[2] = e.H * (w[0] + w[2]) + e.q2h * w[1] + e.u * e.c * dif;
+}
+
+// 2D, direction D (0: x, 1: y): w = L_D x.
+template <int D, typename T>
+__device__ __forceinline__ void l2_apply(const Eig<T>& e, const T* x, T* w) {
+  const T s = e.b1 * (e.q2h * x[0] - e.u * x[1] - e.v * x[2] + x[3]);
+  const T un = D == 0 ? e.u : e.v;
+  const T t = (un * x[0] - x[1 + D]) * e.ic;
+  w[0] = T(0.5) * (s + t);
+  w[1] = x[0] - s;
+  w[2] = D == 0 ? x[2] - e.v * x[0] : x[1] - e.u * x[0];
+  w[3] = T(0.5) * (s - t);
+}
+// 2D, direction D: y = R_D w.
+template <int D, typename T>
+__device__ __forceinline__ void r2_apply(const Eig<T>& e, const T* w, T* y) {
+  const T sum = w[0] + w[1] + w[3];
+  const T dif = w[3] - w[0];
+  const T un = D == 0 ? e.u : e.v;
+  const T ut = D == 0 ? e.v : e.u;   // tangential velocity
+  y[0] = sum;
+  if (D == 0) {
+    y[1] = e.u * sum + e.c * dif;
+    y[2] = e.v * sum + w[2];
+  } else {
+    y[1] = e.u * sum + w[2];
+    y[2] = e.v * sum + e.c * dif;
+  }
+  y[3] = e.H * (w[0] + w[3]) + e.q2h * w[1] + ut * w[2] + un * e.c * dif;
+}
+
+// Flux f(U) and its directional derivative f'(U) V, 1D Euler.
+template <typename T>
+__device__ __forceinline__ void euler1_flux(const T* U, const T* V, T g, T* F, T* H) {
+  const T ir = T(1) / U[0];
+  const T u = U[1] * ir;
+  const T p = (g - T(1)) * (U[2] - T(0.5) * U[1] * u);
+  F[0] = U[1];
+  F[1] = U[1] * u + p;
+  F[2] = u * (U[2] + p);
+  const T du = (V[1] - u * V[0]) * ir;
+  const T dp = (g - T(1)) * (V[2] - u * V[1] + T(0.5) * u * u * V[0]);
+  H[0] = V[1];
+  H[1] = T(2) * u * V[1] - u * u * V[0] + dp;
+  H[2] = du * (U[2] + p) + u * (V[2] + dp);
+}
+
+// 2D Euler, direction D: flux and directional derivatives along V and W.
+template <int D, typename T>
+__device__ __forceinline__ void euler2_flux(const T* U, const T* V, const T* Wv, T g, T* F, T* HV,
+                                            T* HW) {
+  const T ir = T(1) / U[0];
+  const T u = U[1] * ir, v = U[2] * ir;
+  const T gm = g - T(1);
+  const T p = gm * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+  const T un = D == 0 ? u : v;
+  const T mn = U[1 + D];
+  F[0] = mn;
+  F[1] = mn * u + (D == 0 ? p : T(0));
+  F[2] = mn * v + (D == 1 ? p : T(0));
+  F[3] = un * (U[3] + p);
+  const T ek = T(0.5) * (u * u + v * v);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T* X = s == 0 ? V : Wv;
+    T* Hh = s == 0 ? HV : HW;
+    const T du = (X[1] - u * X[0]) * ir;
+    const T dv = (X[2] - v * X[0]) * ir;
+    const T dp = gm * (X[3] - u * X[1] - v * X[2] + ek * X[0]);
+    const T dmn = X[1 + D];
+    const T dun = D == 0 ? du : dv;
+    Hh[0] = dmn;
+    Hh[1] = dmn * u + mn * du + (D == 0 ? dp : T(0));
+    Hh[2] = dmn * v + mn * dv + (D == 1 ? dp : T(0));
+    Hh[3] = dun * (U[3] + p) + un * (X[3] + dp);
+  }
+}
+
+// Spectral radius |u_n| + c (Euler) at a cell average; NaN if non-physical.
+template <typename T>
+__device__ __forceinline__ double euler_radius(T r, T mn, T ekin2, T E, T g) {
+  // ekin2 = |m|^2 (sum of squared momenta)
+  const double rr = (double)r;
+  const double p = ((double)g - 1.0) * ((double)E - 0.5 * (double)ekin2 / rr);
+  if (!(rr > 0.0) || !(p > 0.0)) return __longlong_as_double(0x7ff8000000000000LL);
+  return fabs((double)mn / rr) + sqrt((double)g * p / rr);
+}
+
+// Running max of non-negative doubles through their bit patterns (exact,
+// order independent); NaN bit patterns exceed every finite one.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* slot, double v) {
+  atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(HW_FULL_MASK, v, o);
+    // NaN wins: compare bit patterns of non-negative values
+    v = (unsigned long long)__double_as_longlong(t) > (unsigned long long)__double_as_longlong(v) ? t : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Ghost cells (2 deep) for the fused halo loads.  The map reproduces the
+// definition "x sides filled for interior rows, then y sides for all
+// columns": a cell out of range in x and/or y is resolved axis by axis.
+// ---------------------------------------------------------------------------
+struct GhostMap {
+  int src;      // source index along the axis (valid if !fixed)
+  int flip;     // mirror across this axis
+  int fixed;    // inflow: fixed state
+  int side;     // 0 low, 1 high (for fixed states)
+};
+
+__device__ __forceinline__ GhostMap ghost_map(int c, int n, int bc_lo, int bc_hi) {
+  GhostMap g{c, 0, 0, 0};
+  if (c >= 0 && c < n) return g;
+  const int side = c >= n;
+  const int bc = side ? bc_hi : bc_lo;
+  const int r = side ? c - n : -1 - c;  // ghost depth 0 or 1
+  g.side = side;
+  if (bc == HWENO_BC_PERIODIC) g.src = side ? r : n - 1 - r;
+  else if (bc == HWENO_BC_OUTFLOW) g.src = side ? n - 1 : 0;
+  else if (bc == HWENO_BC_REFLECT) { g.src = side ? n - 1 - r : r; g.flip = 1; }
+  else { g.fixed = 1; g.src = side ? n - 1 : 0; }
+  return g;
+}
+
+// Sign of field (d = 0 average, 1 x-moment, 2 y-moment; component k) under a
+// mirror across a face normal to `axis` (the normal momentum and the
+// moment along the normal change sign).
+__device__ __forceinline__ bool mirror_negates(int eq, int d, int k, int axis) {
+  const bool normal_mom = eq == HWENO_EQ_EULER && k == 1 + axis;
+  const bool normal_der = d == 1 + axis;
+  return normal_mom != normal_der;
+}
+
+}  // namespace hw

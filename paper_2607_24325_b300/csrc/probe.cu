@@ -1,0 +1,58 @@
+// probe.cu -- measured FMA throughput of this GPU (the ALU roofline the
+// stencil kernels are compared against): a grid of 8 resident CTAs per SM,
+// each thread running 8 independent FMA chains, timed with CUDA events.
+#include <cuda_runtime.h>
+
+#include "hweno.h"
+
+namespace {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_probe(T* out, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = T(threadIdx.x) * T(1e-6) + T(k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == T(-1.5)) out[0] = s;  // keeps the chains alive
+}
+
+template <typename T>
+double run_probe(int iters) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  T* out = nullptr;
+  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = sms * 8, threads = 256;
+  k_fma_probe<T><<<blocks, threads>>>(out, iters / 8, T(1.0000001), T(1e-9));  // warm-up
+  cudaEventRecord(e0);
+  k_fma_probe<T><<<blocks, threads>>>(out, iters, T(1.0000001), T(1e-9));
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaError_t err = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (err != cudaSuccess || ms <= 0.f) return -1.0;
+  return 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+}
+
+}  // namespace
+
+extern "C" hweno_status hweno_peak_fma(int precision, double* flops_per_second) {
+  if (!flops_per_second) return HWENO_ERR_ARG;
+  const double f = precision == HWENO_FP64 ? run_probe<double>(1 << 12) : run_probe<float>(1 << 16);
+  *flops_per_second = f;
+  return f > 0.0 ? HWENO_OK : HWENO_ERR_CUDA;
+}

@@ -1,0 +1,567 @@
+// stage2d.cu -- fused 2D HWENO stage kernel (Sec. 2.2 Steps 1-4, Remark 1).
+//
+// A CTA (8 warps) owns a 30 x 30 tile of interior cells.  It stages the
+// 34 x 34 box (tile + 2-cell halo) of every field in shared memory, resolving
+// ghost cells with the boundary map on the way in, then runs
+//   x pass: warp per row, lane l = cell i0-1+l.  Each lane reconstructs its
+//           cell (characteristic-wise with the x eigenvectors of its own
+//           average for Euler), evaluates u, u_x, u_y at the 3 Gauss points
+//           of both x faces, takes its left neighbour's right-face values by
+//           shuffle and forms the Lax-Friedrichs fluxes of its LEFT face
+//           (each interface once); the right-face flux comes from lane+1.
+//           The x part of L and v-hat go to a shared-memory stash.
+//   y pass: the same code on the transposed box (warp per column, lanes
+//           along y).  Transposing swaps the roles of x and y, of v-bar and
+//           w-bar, of the two momentum components and of the stencils S2 and
+//           S4, so the y physics is the x physics in the transposed frame.
+//           It adds the y part of L and applies the RK stage.
+// Interface values, fluxes and L never go through HBM.
+#include <cuda_runtime.h>
+
+#include "hweno_device.cuh"
+#include "kernels.h"
+
+namespace hw {
+
+constexpr int kT2 = 30;           // interior tile edge
+constexpr int kBox = 34;          // tile + 2 halo cells per side
+constexpr int kBP = 35;           // box pitch (odd: conflict-free column walks)
+constexpr int kFS = kBox * kBP;   // box field stride
+constexpr int kSP = 30;           // stash pitch
+constexpr int kSS = kT2 * kSP;    // stash field stride
+constexpr int kThreads2 = 256;
+
+template <int NC>
+constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
+
+template <typename T, int NC>
+constexpr size_t smem_bytes2() {
+  return sizeof(T) * (size_t)(3 * NC * kFS + stash_fields<NC>() * kSS);
+}
+
+// Component of the pass frame holding physical component k (an involution).
+template <int D, int EQ>
+__device__ constexpr int frame_comp(int k) {
+  return (EQ == HWENO_EQ_EULER && D == 1 && (k == 1 || k == 2)) ? 3 - k : k;
+}
+// Box field of frame field (d, k): d = 0 average, 1 moment along the pass
+// normal, 2 moment along the tangent.
+template <int D, int EQ, int NC>
+__device__ constexpr int frame_field(int d, int k) {
+  return (d == 0 ? 0 : (D == 0 ? d : 3 - d)) * NC + frame_comp<D, EQ>(k);
+}
+
+// Value of field f at cell (i, j), ghost cells resolved as "x sides for the
+// interior rows, then y sides for every column".
+template <typename T, int EQ, int NC>
+__device__ __forceinline__ T load_ghost2(const T* __restrict__ in, long long plane, const Grid2& G,
+                                         int f, int i, int j) {
+  const int d = f / NC, k = f % NC;
+  const GhostMap gx = ghost_map(i, G.nx, G.bc[0], G.bc[1]);
+  const GhostMap gy = ghost_map(j, G.ny, G.bc[2], G.bc[3]);
+  if (gy.fixed) return d == 0 ? (T)G.st[2 + gy.side][k] : T(0);
+  T v;
+  if (gx.fixed) {
+    v = d == 0 ? (T)G.st[gx.side][k] : T(0);
+  } else {
+    v = in[f * plane + (long long)gy.src * G.nx + gx.src];
+    if (gx.flip && mirror_negates(EQ, d, k, 0)) v = -v;
+  }
+  if (gy.flip && mirror_negates(EQ, d, k, 1)) v = -v;
+  return v;
+}
+
+// Appendix A (2D): p0 from q1..q17 of the pass frame, the linear p1..p4,
+// the smoothness indicators, the nonlinear weights and the combined
+// polynomial cu of Eq. (hweno-reconstruction-2D) in the basis
+// {1, xi, eta, xi^2, xi eta, eta^2, xi^3, xi^2 eta, xi eta^2, eta^3, xi^4,
+//  xi^3 eta, xi^2 eta^2, xi eta^3, eta^4}.
+template <typename T>
+__device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool lin, T* cu) {
+  const T q1 = q[0], q2 = q[1], q3 = q[2], q4 = q[3], q5 = q[4], q6 = q[5], q7 = q[6], q8 = q[7],
+          q9 = q[8], q10 = q[9], q11 = q[10], q12 = q[11], q13 = q[12], q14 = q[13], q15 = q[14],
+          q16 = q[15], q17 = q[16];
+  const T sc = (q1 + q3) + (q7 + q9);
+  const T cx = (q1 - q3) - (q7 - q9);
+  const T ax = (q1 - q3) + (q7 - q9);
+  const T ay = (q1 + q3) - (q7 + q9);
+  const T ex = q4 + q6, ey = q2 + q8, dxe = q6 - q4, dye = q8 - q2;
+  T c[15];
+  c[0] = (T(5) * sc - T(292) * (ex + ey) + T(4028) * q5 + T(81) * ((q11 - q10) + (q17 - q16))) *
+         T(1.0 / 2880.0);
+  c[1] = (T(2) * ax + T(19) * dxe - T(6) * (q10 + q11) + T(3) * (q12 + q13)) * T(1.0 / 24.0);
+  c[2] = (T(2) * ay + T(19) * dye + T(3) * (q14 + q15) - T(6) * (q16 + q17)) * T(1.0 / 24.0);
+  c[3] = (T(2) * ey + T(62) * ex - sc - T(124) * q5 + T(18) * (q10 - q11)) * T(1.0 / 48.0);
+  c[4] = (T(-3) * cx - T(5) * ((q12 - q13) + (q14 - q15))) * T(0.125);
+  c[5] = (T(2) * ex + T(62) * ey - sc - T(124) * q5 + T(18) * (q16 - q17)) * T(1.0 / 48.0);
+  c[6] = (T(4) * ((q10 + q11) - dxe) - ax - T(2) * (q12 + q13)) * T(0.05);
+  c[7] = ((q7 + q9 - T(2) * q8) - (q1 + q3 - T(2) * q2)) * T(0.25);
+  c[8] = ((q3 + q9 - T(2) * q6) - (q1 + q7 - T(2) * q4)) * T(0.25);
+  c[9] = (T(4) * ((q16 + q17) - dye) - ay - T(2) * (q14 + q15)) * T(0.05);
+  c[10] = (T(4) * q5 - T(2) * ex + (q11 - q10)) * T(0.25);
+  c[11] = (cx + T(2) * (q12 - q13)) * T(0.25);
+  c[12] = (sc - T(2) * (ex + ey) + T(4) * q5) * T(0.25);
+  c[13] = (cx + T(2) * (q14 - q15)) * T(0.25);
+  c[14] = (T(4) * q5 - T(2) * ey + (q17 - q16)) * T(0.25);
+  if (lin) {
+#pragma unroll
+    for (int l = 0; l < 15; ++l) cu[l] = c[l];
+    return;
+  }
+  // p1..p4 = q5 + sx xi + sy eta on S1 {W,S}, S2 {E,S}, S3 {E,N}, S4 {W,N}
+  const T dW = q5 - q4, dE = q6 - q5, dS = q5 - q2, dN = q8 - q5;
+  const T b1 = dW * dW + dS * dS, b2 = dE * dE + dS * dS, b3 = dE * dE + dN * dN, b4 = dW * dW + dN * dN;
+  const T b0 = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] + T(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
+               T(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
+               T(576) * (c[10] * c[10] + c[14] * c[14]) + T(16) * c[12] * c[12];
+  const T tau = T(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
+  const T t2 = tau * tau;
+  const T e0 = wtilde(w.g[0], t2, b0, w), e1 = wtilde(w.g[1], t2, b1, w), e2 = wtilde(w.g[2], t2, b2, w),
+          e3 = wtilde(w.g[3], t2, b3, w), e4 = wtilde(w.g[4], t2, b4, w);
+  const T inv = T(1) / ((e0 + e1) + (e2 + e3) + e4);
+  const T r = e0 * inv * w.inv_g0;
+  const T w1 = e1 * inv, w2 = e2 * inv, w3 = e3 * inv, w4 = e4 * inv;
+  const T gs = (w.g[1] + w.g[2]) + (w.g[3] + w.g[4]);
+  const T ws = (w1 + w2) + (w3 + w4);
+  cu[0] = r * (c[0] - gs * q5) + ws * q5;
+  cu[1] = r * (c[1] - ((w.g[1] + w.g[4]) * dW + (w.g[2] + w.g[3]) * dE)) + ((w1 + w4) * dW + (w2 + w3) * dE);
+  cu[2] = r * (c[2] - ((w.g[1] + w.g[2]) * dS + (w.g[3] + w.g[4]) * dN)) + ((w1 + w2) * dS + (w3 + w4) * dN);
+#pragma unroll
+  for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
+}
+
+// Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)
+// of the pass frame: u, d/dxi u, d/deta u.
+template <typename T>
+struct FacePts { T u[3], un[3], ut[3]; };
+
+template <typename T>
+__device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
+  const T s = T(0.38729833462074168852), s2 = T(0.15), s3 = s * T(0.15), s4 = T(0.0225);
+  const T A0 = (c[0] + T(0.25) * c[3] + T(0.0625) * c[10]) + sgn * (T(0.5) * c[1] + T(0.125) * c[6]);
+  const T A1 = (c[2] + T(0.25) * c[7]) + sgn * (T(0.5) * c[4] + T(0.125) * c[11]);
+  const T A2 = (c[5] + T(0.25) * c[12]) + sgn * (T(0.5) * c[8]);
+  const T A3 = c[9] + sgn * (T(0.5) * c[13]);
+  const T A4 = c[14];
+  const T B0 = (c[1] + T(0.75) * c[6]) + sgn * (c[3] + T(0.5) * c[10]);
+  const T B1 = (c[4] + T(0.75) * c[11]) + sgn * c[7];
+  const T B2 = c[8] + sgn * c[12];
+  const T B3 = c[13];
+  const T ue = A0 + A2 * s2 + A4 * s4, uo = A1 * s + A3 * s3;
+  const T ne = B0 + B2 * s2, no = B1 * s + B3 * s3;
+  const T te = A1 + T(3) * A3 * s2, to = T(2) * A2 * s + T(4) * A4 * s3;
+  o.u[0] = ue - uo; o.u[1] = A0; o.u[2] = ue + uo;
+  o.un[0] = ne - no; o.un[1] = B0; o.un[2] = ne + no;
+  o.ut[0] = te - to; o.ut[1] = A1; o.ut[2] = te + to;
+}
+
+// Lax-Friedrichs fluxes of the pass-frame x physics at one point:
+// f, f'(u) v (normal moment), f'(u) w (tangential moment).
+template <typename T, int NC, int EQ>
+__device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, const T* Up, const T* Vp,
+                                         const T* Wp, T alpha, T g, T adv, T* fu, T* fv, T* fw) {
+  T Fm[NC], Fp[NC], HVm[NC], HVp[NC], HWm[NC], HWp[NC];
+  if constexpr (EQ == HWENO_EQ_EULER) {
+    euler2_flux<0>(Um, Vm, Wm, g, Fm, HVm, HWm);
+    euler2_flux<0>(Up, Vp, Wp, g, Fp, HVp, HWp);
+  } else if constexpr (EQ == HWENO_EQ_BURGERS) {
+    Fm[0] = T(0.5) * Um[0] * Um[0]; HVm[0] = Um[0] * Vm[0]; HWm[0] = Um[0] * Wm[0];
+    Fp[0] = T(0.5) * Up[0] * Up[0]; HVp[0] = Up[0] * Vp[0]; HWp[0] = Up[0] * Wp[0];
+  } else {
+    Fm[0] = adv * Um[0]; HVm[0] = adv * Vm[0]; HWm[0] = adv * Wm[0];
+    Fp[0] = adv * Up[0]; HVp[0] = adv * Vp[0]; HWp[0] = adv * Wp[0];
+  }
+  const T ha = T(0.5) * alpha;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    fu[k] = T(0.5) * (Fm[k] + Fp[k]) - ha * (Up[k] - Um[k]);
+    fv[k] = T(0.5) * (HVm[k] + HVp[k]) - ha * (Vp[k] - Vm[k]);
+    fw[k] = T(0.5) * (HWm[k] + HWp[k]) - ha * (Wp[k] - Wm[k]);
+  }
+}
+
+// One directional pass for the lane's cell at box index bidx.  Returns the
+// Gauss-summed fluxes of the cell's low face (frame components) and the
+// limited derivative along the pass normal.  All 32 lanes must call it.
+template <typename T, int EQ, bool CHR, int D>
+__device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, const WeightsT<T>& w,
+                                       bool lin, T ihn, T iht, T alpha, T g, T adv, T* Fu, T* Fv, T* Fw,
+                                       T* vh) {
+  constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
+  constexpr int SN = D == 0 ? 1 : kBP;
+  constexpr int ST = D == 0 ? kBP : 1;
+  const int o9[9] = {-SN - ST, -ST, SN - ST, -SN, 0, SN, -SN + ST, ST, SN + ST};
+  const int o4[4] = {-SN, SN, -ST, ST};
+  T cu[NC][15];
+  Eig<T> e{};
+  const bool chr = CHR && !lin;
+  if (chr) {
+    T x0[4];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x0[k] = box[frame_field<D, EQ, NC>(0, k) * kFS + bidx];
+    e = eig2<T>(x0[0], x0[1], x0[2], x0[3], g);
+  }
+  {
+    T q[NC][17];
+#pragma unroll
+    for (int s = 0; s < 17; ++s) {
+      T x[NC];
+      const int dd = s < 9 ? 0 : (s < 13 ? 1 : 2);
+      const int off = s < 9 ? o9[s] : o4[(s - 9) & 3];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) x[k] = box[frame_field<D, EQ, NC>(dd, k) * kFS + bidx + off];
+      if constexpr (CHR) {
+        if (chr) {
+          T y[4];
+          l2_apply<0>(e, x, y);
+#pragma unroll
+          for (int k = 0; k < NC; ++k) x[k] = y[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NC; ++k) q[k][s] = x[k];
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) recon2<T>(q[k], w, lin, cu[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) { Fu[k] = T(0); Fv[k] = T(0); Fw[k] = T(0); vh[k] = T(0); }
+  const T sig[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+  FacePts<T> fr[NC], fl[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    face_points<T>(cu[k], T(1), fr[k]);
+    face_points<T>(cu[k], T(-1), fl[k]);
+  }
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    T UR[NC], VR[NC], WR[NC], UL[NC], VL[NC], WL[NC];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      T u[NC], un[NC], ut[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        const FacePts<T>& fp = side == 0 ? fr[k] : fl[k];
+        u[k] = fp.u[mu]; un[k] = fp.un[mu]; ut[k] = fp.ut[mu];
+      }
+      T* Uo = side == 0 ? UR : UL;
+      T* Vo = side == 0 ? VR : VL;
+      T* Wo = side == 0 ? WR : WL;
+      if constexpr (CHR) {
+        if (chr) {
+          r2_apply<0>(e, u, Uo);
+          r2_apply<0>(e, un, Vo);
+          r2_apply<0>(e, ut, Wo);
+        } else {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
+      }
+#pragma unroll
+      for (int k = 0; k < NC; ++k) { Vo[k] *= ihn; Wo[k] *= iht; }
+    }
+    // left neighbour's right-face state at this Gauss point
+    T Um[NC], Vm[NC], Wm[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Um[k] = __shfl_up_sync(HW_FULL_MASK, UR[k], 1);
+      Vm[k] = __shfl_up_sync(HW_FULL_MASK, VR[k], 1);
+      Wm[k] = __shfl_up_sync(HW_FULL_MASK, WR[k], 1);
+    }
+    T fu[NC], fv[NC], fw[NC];
+    lf_point<T, NC, EQ>(Um, Vm, Wm, UL, VL, WL, alpha, g, adv, fu, fv, fw);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      Fu[k] += sig[mu] * fu[k];
+      Fv[k] += sig[mu] * fv[k];
+      Fw[k] += sig[mu] * fw[k];
+      vh[k] += sig[mu] * (UR[k] - UL[k]);
+    }
+  }
+}
+
+template <typename T, int EQ, bool CHR>
+__global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
+  constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
+  constexpr int NF = 3 * NC;
+  extern __shared__ __align__(16) unsigned char hw_smem[];
+  T* box = reinterpret_cast<T*>(hw_smem);
+  T* stash = box + NF * kFS;
+  const T* __restrict__ in = static_cast<const T*>(a.in);
+  const T* base = static_cast<const T*>(a.base);  // aliases out at stage 3
+  T* out = static_cast<T*>(a.out);
+  T* __restrict__ hat = static_cast<T*>(a.hat);
+  const Grid2 G = a.grid;
+  const long long plane = a.plane;
+  double dt = 0.0, axd, ayd;
+  if (a.stage == 0) {
+    axd = a.ax_op;
+    ayd = a.ay_op;
+  } else {
+    if (a.ctl->done) return;
+    dt = a.ctl->dt;
+    axd = a.ctl->ax;
+    ayd = a.ctl->ay;
+  }
+  const WeightsT<T> wx = make_weights<T>(a.wp);
+  WeightsT<T> wy = wx;  // transposed frame: S2 <-> S4
+  wy.g[2] = wx.g[4];
+  wy.g[4] = wx.g[2];
+  const bool lin = a.wp.linear != 0;
+  const T g = (T)a.gamma_gas;
+  const T idx = (T)(1.0 / G.dx), idy = (T)(1.0 / G.dy);
+  const T dyx = (T)(G.dy / G.dx), dxy = (T)(G.dx / G.dy);
+  const T tdt = (T)dt;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int tiles_x = (G.nx + kT2 - 1) / kT2;
+  const int ntiles = tiles_x * ((G.ny + kT2 - 1) / kT2);
+  double radx = 0.0, rady = 0.0;
+
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int i0 = (tile % tiles_x) * kT2, j0 = (tile / tiles_x) * kT2;
+    __syncthreads();
+    const bool inner = i0 >= 2 && j0 >= 2 && i0 + kBox - 2 <= G.nx && j0 + kBox - 2 <= G.ny;
+    for (int e = threadIdx.x; e < NF * kBox * kBox; e += blockDim.x) {
+      const int f = e / (kBox * kBox), rem = e - f * (kBox * kBox);
+      const int rr = rem / kBox, cc = rem - rr * kBox;
+      int i = i0 - 2 + cc, j = j0 - 2 + rr;
+      T v;
+      if (inner) {
+        v = in[f * plane + (long long)j * G.nx + i];
+      } else {
+        i = min(max(i, -2), G.nx + 1);
+        j = min(max(j, -2), G.ny + 1);
+        if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
+        else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j);
+      }
+      box[f * kFS + rr * kBP + cc] = v;
+    }
+    __syncthreads();
+
+    // ---- x pass: one row per warp iteration, lane l <-> cell i0-1+l ----
+    for (int r = warp; r < kT2; r += nwarps) {
+      if (j0 + r >= G.ny) break;
+      T Fu[NC], Fv[NC], Fw[NC], vh[NC];
+      pass2d<T, EQ, CHR, 0>(box, (r + 2) * kBP + lane + 1, wx, lin, idx, idy, (T)axd, g, (T)a.adv_x, Fu,
+                            Fv, Fw, vh);
+      T Gu[NC], Gv[NC], Gw[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
+        Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
+        Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
+      }
+      if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
+        const int sidx = r * kSP + lane - 1;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          stash[(0 * NC + k) * kSS + sidx] = -(Gu[k] - Fu[k]) * idx;
+          stash[(1 * NC + k) * kSS + sidx] = -(Gv[k] - Fv[k]);
+          stash[(2 * NC + k) * kSS + sidx] = -(Gw[k] - Fw[k]) * dyx;
+          stash[(3 * NC + k) * kSS + sidx] = vh[k];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- y pass on the transposed box: one column per warp iteration ----
+    for (int c = warp; c < kT2; c += nwarps) {
+      const int i = i0 + c;
+      if (i >= G.nx) break;
+      T Fu[NC], Fv[NC], Fw[NC], vh[NC];
+      pass2d<T, EQ, CHR, 1>(box, (lane + 1) * kBP + c + 2, wy, lin, idy, idx, (T)ayd, g, (T)a.adv_y, Fu,
+                            Fv, Fw, vh);
+      T Gu[NC], Gv[NC], Gw[NC];
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
+        Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
+        Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
+      }
+      const int j = j0 - 1 + lane;
+      if (lane >= 1 && lane <= kT2 && j < G.ny) {
+        const int sidx = (lane - 1) * kSP + c;
+        const long long p = (long long)j * G.nx + i;
+        T nu[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+          const int kk = frame_comp<1, EQ>(k);
+          const T Lu = stash[(0 * NC + k) * kSS + sidx] - (Gu[kk] - Fu[kk]) * idy;
+          const T Lv = stash[(1 * NC + k) * kSS + sidx] - (Gw[kk] - Fw[kk]) * dxy;
+          const T Lw = stash[(2 * NC + k) * kSS + sidx] - (Gv[kk] - Fv[kk]);
+          const T vx = stash[(3 * NC + k) * kSS + sidx];
+          const T wyv = vh[kk];
+          const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
+          const long long hv = k * plane + p, hw_ = (NC + k) * plane + p;
+          if (a.stage == 0) {
+            out[iu] = Lu; out[iv] = Lv; out[iw] = Lw;
+            hat[hv] = vx; hat[hw_] = wyv;
+          } else {
+            const T ub = box[k * kFS + (lane + 1) * kBP + c + 2];
+            const T su = ub + tdt * Lu, sv = vx + tdt * Lv, sw = wyv + tdt * Lw;
+            if (a.stage == 1) {
+              out[iu] = su; out[iv] = sv; out[iw] = sw;
+              hat[hv] = vx; hat[hw_] = wyv;
+            } else if (a.stage == 2) {
+              out[iu] = T(0.75) * base[iu] + T(0.25) * su;
+              out[iv] = T(0.75) * hat[hv] + T(0.25) * sv;
+              out[iw] = T(0.75) * hat[hw_] + T(0.25) * sw;
+            } else {
+              nu[k] = base[iu] * T(1.0 / 3.0) + T(2.0 / 3.0) * su;
+              out[iv] = hat[hv] * T(1.0 / 3.0) + T(2.0 / 3.0) * sv;
+              out[iw] = hat[hw_] * T(1.0 / 3.0) + T(2.0 / 3.0) * sw;
+              out[iu] = nu[k];
+            }
+          }
+        }
+        if (a.stage == 3) {
+          if constexpr (EQ == HWENO_EQ_EULER) {
+            const T m2 = nu[1] * nu[1] + nu[2] * nu[2];
+            const double rx = euler_radius<T>(nu[0], nu[1], m2, nu[3], g);
+            const double ry = euler_radius<T>(nu[0], nu[2], m2, nu[3], g);
+            radx = (unsigned long long)__double_as_longlong(rx) > (unsigned long long)__double_as_longlong(radx) ? rx : radx;
+            rady = (unsigned long long)__double_as_longlong(ry) > (unsigned long long)__double_as_longlong(rady) ? ry : rady;
+          } else if constexpr (EQ == HWENO_EQ_BURGERS) {
+            const double rr = fabs((double)nu[0]);
+            radx = (unsigned long long)__double_as_longlong(rr) > (unsigned long long)__double_as_longlong(radx) ? rr : radx;
+            rady = radx;
+          } else {
+            radx = fabs(a.adv_x);
+            rady = fabs(a.adv_y);
+          }
+        }
+      }
+    }
+  }
+  if (a.stage == 3) {
+    radx = warp_max(radx);
+    rady = warp_max(rady);
+    if (lane == 0) {
+      atomic_max_nonneg(&a.ctl->amax_x, radx);
+      atomic_max_nonneg(&a.ctl->amax_y, rady);
+    }
+  }
+}
+
+template <typename T, int EQ>
+__global__ void __launch_bounds__(256) k_alpha2d(const T* __restrict__ U, long long plane, double gamma_gas,
+                                                 double adv_x, double adv_y, Ctl* ctl) {
+  double rx = 0.0, ry = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < plane;
+       c += (long long)gridDim.x * blockDim.x) {
+    double a, b;
+    if constexpr (EQ == HWENO_EQ_EULER) {
+      const T r = U[c], mx = U[plane + c], my = U[2 * plane + c], E = U[3 * plane + c];
+      const T m2 = mx * mx + my * my;
+      a = euler_radius<T>(r, mx, m2, E, (T)gamma_gas);
+      b = euler_radius<T>(r, my, m2, E, (T)gamma_gas);
+    } else if constexpr (EQ == HWENO_EQ_BURGERS) {
+      a = b = fabs((double)U[c]);
+    } else {
+      a = fabs(adv_x);
+      b = fabs(adv_y);
+    }
+    rx = (unsigned long long)__double_as_longlong(a) > (unsigned long long)__double_as_longlong(rx) ? a : rx;
+    ry = (unsigned long long)__double_as_longlong(b) > (unsigned long long)__double_as_longlong(ry) ? b : ry;
+  }
+  rx = warp_max(rx);
+  ry = warp_max(ry);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(&ctl->amax_x, rx);
+    atomic_max_nonneg(&ctl->amax_y, ry);
+  }
+}
+
+template <typename T, int EQ, bool CHR>
+struct Launch2 {
+  static int per_sm;  // resident CTAs per SM, 0 until prepared
+  static cudaError_t prepare() {
+    if (per_sm > 0) return cudaSuccess;
+    constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
+    constexpr size_t smem = smem_bytes2<T, NC>();
+    cudaError_t e = cudaFuncSetAttribute(k_stage2d<T, EQ, CHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR>, kThreads2, smem);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    per_sm = n;
+    return cudaSuccess;
+  }
+  static cudaError_t go(const Stage2Args& a, int num_sms, cudaStream_t st) {
+    constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
+    constexpr size_t smem = smem_bytes2<T, NC>();
+    if (per_sm == 0) {
+      cudaError_t e = prepare();
+      if (e != cudaSuccess) return e;
+    }
+    const long long tiles = (long long)((a.grid.nx + kT2 - 1) / kT2) * ((a.grid.ny + kT2 - 1) / kT2);
+    long long blocks = (long long)num_sms * per_sm;
+    if (blocks > tiles) blocks = tiles;
+    k_stage2d<T, EQ, CHR><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
+    return cudaGetLastError();
+  }
+};
+template <typename T, int EQ, bool CHR>
+int Launch2<T, EQ, CHR>::per_sm = 0;
+
+template <typename T, int EQ, bool CHR>
+static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st) {
+  return Launch2<T, EQ, CHR>::go(a, num_sms, st);
+}
+
+template <typename T>
+static cudaError_t prep2(int equation, bool chr) {
+  if (equation == HWENO_EQ_EULER)
+    return chr ? Launch2<T, HWENO_EQ_EULER, true>::prepare() : Launch2<T, HWENO_EQ_EULER, false>::prepare();
+  if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false>::prepare();
+  return Launch2<T, HWENO_EQ_ADVECTION, false>::prepare();
+}
+
+cudaError_t prepare_stage2d(int precision, int equation, int charwise) {
+  const bool chr = equation == HWENO_EQ_EULER && charwise;
+  // the linear-weight path of a characteristic solver runs the same kernel
+  return precision == HWENO_FP64 ? prep2<double>(equation, chr) : prep2<float>(equation, chr);
+}
+
+cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a, int num_sms,
+                           cudaStream_t st) {
+  const bool chr = equation == HWENO_EQ_EULER && charwise;
+  if (precision == HWENO_FP64) {
+    if (equation == HWENO_EQ_EULER) return chr ? go2<double, HWENO_EQ_EULER, true>(a, num_sms, st)
+                                               : go2<double, HWENO_EQ_EULER, false>(a, num_sms, st);
+    if (equation == HWENO_EQ_BURGERS) return go2<double, HWENO_EQ_BURGERS, false>(a, num_sms, st);
+    return go2<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+  }
+  if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true>(a, num_sms, st)
+                                             : go2<float, HWENO_EQ_EULER, false>(a, num_sms, st);
+  if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false>(a, num_sms, st);
+  return go2<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+}
+
+cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane, double gamma_gas,
+                           double adv_x, double adv_y, Ctl* ctl, int num_sms, cudaStream_t st) {
+  long long blocks = (plane + 255) / 256;
+  if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+  if (blocks < 1) blocks = 1;
+#define HW_A2(T, EQ) k_alpha2d<T, EQ><<<(unsigned)blocks, 256, 0, st>>>( \
+    static_cast<const T*>(U), plane, gamma_gas, adv_x, adv_y, ctl)
+  if (precision == HWENO_FP64) {
+    if (equation == HWENO_EQ_EULER) HW_A2(double, HWENO_EQ_EULER);
+    else if (equation == HWENO_EQ_BURGERS) HW_A2(double, HWENO_EQ_BURGERS);
+    else HW_A2(double, HWENO_EQ_ADVECTION);
+  } else {
+    if (equation == HWENO_EQ_EULER) HW_A2(float, HWENO_EQ_EULER);
+    else if (equation == HWENO_EQ_BURGERS) HW_A2(float, HWENO_EQ_BURGERS);
+    else HW_A2(float, HWENO_EQ_ADVECTION);
+  }
+#undef HW_A2
+  return cudaGetLastError();
+}
+
+}  // namespace hw

@@ -1,0 +1,430 @@
+"""Thin Python binding of libhweno (``include/hweno.h``).
+
+Argument marshalling only: every step of the scheme runs in the CUDA
+kernels behind the C ABI.  The module-level functions carry the C entry
+points' names; ``Solver`` and ``Batch`` are small conveniences over them.
+Device buffers are torch CUDA tensors; host buffers are numpy arrays (or CPU
+tensors).  If ``libhweno.so`` is missing this module raises -- there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhweno.so")
+
+HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL = 0, 1, 2, 3
+HWENO_ERR_TIMEOUT, HWENO_ERR_OOM, HWENO_ERR_STATE = 4, 5, 6
+EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+DT_CFL, DT_CFL_DX53 = 0, 1
+
+# every extern "C" symbol include/hweno.h declares
+EXPORTS = (
+    "hweno_last_error", "hweno_version", "hweno_create", "hweno_destroy", "hweno_stream",
+    "hweno_shape", "hweno_set_state", "hweno_get_state", "hweno_alpha", "hweno_apply_operator",
+    "hweno_step", "hweno_advance", "hweno_set_profiling", "hweno_profile", "hweno_peak_fma",
+    "hweno_batch_create", "hweno_batch_destroy",
+    "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
+    "hweno_batch_advance", "hweno_batch_apply_operator",
+)
+
+
+class hweno_config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+        ("xlo", C.c_double), ("xhi", C.c_double), ("ylo", C.c_double), ("yhi", C.c_double),
+        ("equation", C.c_int), ("adv_x", C.c_double), ("adv_y", C.c_double), ("gamma_gas", C.c_double),
+        ("lin_w", C.c_double * 5), ("eps", C.c_double), ("weight_pow", C.c_int),
+        ("charwise", C.c_int), ("linear_weights", C.c_int), ("cfl", C.c_double), ("dt_rule", C.c_int),
+        ("bc", C.c_int * 4), ("bc_state", (C.c_double * 4) * 4), ("precision", C.c_int),
+    ]
+
+
+@dataclass
+class Config:
+    """Python mirror of ``hweno_config`` with the paper's defaults."""
+    dim: int = 1
+    nx: int = 16
+    ny: int = 1
+    xlo: float = 0.0
+    xhi: float = 1.0
+    ylo: float = 0.0
+    yhi: float = 1.0
+    equation: int = EQ_ADVECTION
+    adv_x: float = 1.0
+    adv_y: float = 1.0
+    gamma_gas: float = 1.4
+    lin_w: tuple = (0.995, 0.0025, 0.0025)
+    eps: float = 1e-8
+    weight_pow: int = 1
+    charwise: int = 1
+    linear_weights: int = 0
+    cfl: float = 0.6
+    dt_rule: int = DT_CFL
+    bc: tuple = (BC_PERIODIC,) * 4
+    bc_state: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])
+    precision: int = FP64
+
+    @property
+    def ncomp(self) -> int:
+        return 1 if self.equation != EQ_EULER else (3 if self.dim == 1 else 4)
+
+    @property
+    def nfields(self) -> int:
+        return self.ncomp * (self.dim + 1)
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * (self.ny if self.dim == 2 else 1)
+
+    def to_c(self) -> hweno_config:
+        c = hweno_config()
+        c.dim, c.nx, c.ny = self.dim, self.nx, self.ny if self.dim == 2 else 1
+        c.xlo, c.xhi, c.ylo, c.yhi = self.xlo, self.xhi, self.ylo, self.yhi
+        c.equation, c.adv_x, c.adv_y, c.gamma_gas = self.equation, self.adv_x, self.adv_y, self.gamma_gas
+        w = list(self.lin_w) + [0.0] * (5 - len(self.lin_w))
+        for k in range(5):
+            c.lin_w[k] = w[k]
+        c.eps, c.weight_pow, c.charwise, c.linear_weights = self.eps, self.weight_pow, self.charwise, self.linear_weights
+        c.cfl, c.dt_rule, c.precision = self.cfl, self.dt_rule, self.precision
+        for k in range(4):
+            c.bc[k] = self.bc[k]
+            for q in range(4):
+                c.bc_state[k][q] = self.bc_state[k][q]
+        return c
+
+
+class HwenoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libhweno status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libhweno.so (never a fallback: raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, cp = C.c_void_p, C.POINTER(hweno_config)
+    L.hweno_last_error.restype = C.c_char_p
+    L.hweno_version.restype = C.c_char_p
+    L.hweno_create.argtypes = [cp, vp, C.POINTER(vp)]
+    L.hweno_destroy.argtypes = [vp]
+    L.hweno_destroy.restype = None
+    L.hweno_stream.argtypes = [vp]
+    L.hweno_stream.restype = vp
+    L.hweno_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_size_t)]
+    L.hweno_set_state.argtypes = [vp, vp, C.c_int]
+    L.hweno_get_state.argtypes = [vp, vp, C.c_int]
+    L.hweno_alpha.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.hweno_apply_operator.argtypes = [vp, C.c_double, C.c_double, vp, vp]
+    L.hweno_step.argtypes = [vp, C.c_double, C.c_double, C.c_double]
+    L.hweno_advance.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.hweno_set_profiling.argtypes = [vp, C.c_int]
+    L.hweno_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    L.hweno_peak_fma.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    L.hweno_batch_create.argtypes = [C.c_int, cp, vp, C.POINTER(vp)]
+    L.hweno_batch_destroy.argtypes = [vp]
+    L.hweno_batch_destroy.restype = None
+    L.hweno_batch_stream.argtypes = [vp]
+    L.hweno_batch_stream.restype = vp
+    L.hweno_batch_layout.argtypes = [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+    L.hweno_batch_set_state.argtypes = [vp, vp, C.c_int]
+    L.hweno_batch_get_state.argtypes = [vp, vp, C.c_int]
+    L.hweno_batch_advance.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int)]
+    L.hweno_batch_apply_operator.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st != HWENO_OK:
+        raise HwenoError(st, load().hweno_last_error().decode())
+
+
+def _buf(x):
+    """(pointer, on_device) of a torch tensor or numpy array (contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, 0
+    import torch
+    assert isinstance(x, torch.Tensor) and x.is_contiguous()
+    return x.data_ptr(), 1 if x.is_cuda else 0
+
+
+def _current_stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ---- module-level functions with the C entry points' names ----
+def hweno_version() -> str:
+    return load().hweno_version().decode()
+
+
+def hweno_last_error() -> str:
+    return load().hweno_last_error().decode()
+
+
+def hweno_create(cfg: Config, stream=None):
+    h = C.c_void_p()
+    c = cfg.to_c()
+    _check(load().hweno_create(C.byref(c), stream if stream is not None else _current_stream(), C.byref(h)))
+    return h
+
+
+def hweno_destroy(h):
+    load().hweno_destroy(h)
+
+
+def hweno_stream(h) -> int:
+    return load().hweno_stream(h)
+
+
+def hweno_set_state(h, U):
+    p, dev = _buf(U)
+    _check(load().hweno_set_state(h, C.c_void_p(p), dev))
+
+
+def hweno_get_state(h, U):
+    p, dev = _buf(U)
+    _check(load().hweno_get_state(h, C.c_void_p(p), dev))
+
+
+def hweno_alpha(h):
+    ax, ay = C.c_double(), C.c_double()
+    _check(load().hweno_alpha(h, C.byref(ax), C.byref(ay)))
+    return ax.value, ay.value
+
+
+def hweno_apply_operator(h, alpha_x, alpha_y, L_out, dhat_out):
+    pl, _ = _buf(L_out)
+    pd, _ = _buf(dhat_out)
+    _check(load().hweno_apply_operator(h, alpha_x, alpha_y, C.c_void_p(pl), C.c_void_p(pd)))
+
+
+def hweno_step(h, dt, alpha_x, alpha_y=0.0):
+    _check(load().hweno_step(h, dt, alpha_x, alpha_y))
+
+
+def hweno_advance(h, t_final, max_steps=2**31 - 1):
+    t, n = C.c_double(), C.c_int()
+    _check(load().hweno_advance(h, t_final, int(max_steps), C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def hweno_set_profiling(h, enable: bool):
+    _check(load().hweno_set_profiling(h, 1 if enable else 0))
+
+
+def hweno_profile(h):
+    ms, n, k = C.c_double(), C.c_longlong(), C.c_longlong()
+    _check(load().hweno_profile(h, C.byref(ms), C.byref(n), C.byref(k)))
+    return ms.value, n.value, k.value
+
+
+def hweno_peak_fma(precision: int) -> float:
+    f = C.c_double()
+    _check(load().hweno_peak_fma(precision, C.byref(f)))
+    return f.value
+
+
+def hweno_batch_create(cfgs, stream=None):
+    arr = (hweno_config * len(cfgs))(*[c.to_c() for c in cfgs])
+    h = C.c_void_p()
+    _check(load().hweno_batch_create(len(cfgs), arr, stream if stream is not None else _current_stream(),
+                                     C.byref(h)))
+    return h
+
+
+def hweno_batch_destroy(h):
+    load().hweno_batch_destroy(h)
+
+
+def hweno_batch_stream(h) -> int:
+    return load().hweno_batch_stream(h)
+
+
+def hweno_batch_layout(h, n):
+    total = C.c_size_t()
+    offs = (C.c_size_t * (n + 1))()
+    _check(load().hweno_batch_layout(h, C.byref(total), offs))
+    return total.value, np.array(offs[:], dtype=np.int64)
+
+
+def hweno_batch_set_state(h, U):
+    p, dev = _buf(U)
+    _check(load().hweno_batch_set_state(h, C.c_void_p(p), dev))
+
+
+def hweno_batch_get_state(h, U):
+    p, dev = _buf(U)
+    _check(load().hweno_batch_get_state(h, C.c_void_p(p), dev))
+
+
+def hweno_batch_advance(h, t_final, max_steps=2**31 - 1):
+    n = len(t_final)
+    tf = (C.c_double * n)(*[float(x) for x in t_final])
+    t = (C.c_double * n)()
+    s = (C.c_int * n)()
+    _check(load().hweno_batch_advance(h, tf, int(max_steps), t, s))
+    return np.array(t[:]), np.array(s[:])
+
+
+def hweno_batch_apply_operator(h, alpha, L_out, dhat_out):
+    n = len(alpha)
+    a = (C.c_double * n)(*[float(x) for x in alpha])
+    pl, _ = _buf(L_out)
+    pd, _ = _buf(dhat_out)
+    _check(load().hweno_batch_apply_operator(h, a, C.c_void_p(pl), C.c_void_p(pd)))
+
+
+# ---- conveniences ----
+class Solver:
+    """One grid.  State tensors are [nf, ny, nx] (2D) or [nf, nx] (1D)."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        self.cfg = cfg
+        self.dtype = torch.float64 if cfg.precision == FP64 else torch.float32
+        self.h = hweno_create(cfg, stream)
+        self.shape = (cfg.nfields, cfg.ny, cfg.nx) if cfg.dim == 2 else (cfg.nfields, cfg.nx)
+
+    def close(self):
+        if self.h is not None:
+            hweno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self) -> int:
+        return hweno_stream(self.h)
+
+    def set_state(self, U):
+        import torch
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64 if self.cfg.precision == FP64 else np.float32)
+        else:
+            U = U.to(self.dtype).contiguous()
+        assert tuple(U.shape) == self.shape, (U.shape, self.shape)
+        hweno_set_state(self.h, U)
+        self._keep = U
+
+    def get_state(self, device: bool = True):
+        import torch
+        if device:
+            out = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        else:
+            out = np.empty(self.shape, dtype=np.float64 if self.cfg.precision == FP64 else np.float32)
+        hweno_get_state(self.h, out)
+        return out
+
+    def alpha(self):
+        return hweno_alpha(self.h)
+
+    def apply_operator(self, alpha_x, alpha_y=0.0):
+        import torch
+        L = torch.empty(self.shape, dtype=self.dtype, device="cuda")
+        nd = self.cfg.ncomp * self.cfg.dim
+        D = torch.empty((nd,) + self.shape[1:], dtype=self.dtype, device="cuda")
+        hweno_apply_operator(self.h, alpha_x, alpha_y, L, D)
+        return L, D
+
+    def step(self, dt, alpha_x, alpha_y=0.0):
+        hweno_step(self.h, dt, alpha_x, alpha_y)
+
+    def advance(self, t_final, max_steps=2**31 - 1):
+        return hweno_advance(self.h, t_final, max_steps)
+
+    def set_profiling(self, enable: bool = True):
+        hweno_set_profiling(self.h, enable)
+
+    def profile(self):
+        """(summed stage-kernel ms, stage launches, kernels launched by advance)."""
+        return hweno_profile(self.h)
+
+
+class Batch:
+    """Independent 1D problems of uneven sizes, advanced together."""
+
+    def __init__(self, cfgs, stream=None):
+        import torch
+        self.cfgs = list(cfgs)
+        self.n = len(self.cfgs)
+        c0 = self.cfgs[0]
+        self.dtype = torch.float64 if c0.precision == FP64 else torch.float32
+        self.h = hweno_batch_create(self.cfgs, stream)
+        self.total, self.offsets = hweno_batch_layout(self.h, self.n)
+        self.nf = c0.nfields
+
+    def close(self):
+        if self.h is not None:
+            hweno_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self) -> int:
+        return hweno_batch_stream(self.h)
+
+    def pack(self, states):
+        """Concatenate per-instance [nf, n_k] arrays into [nf, total]."""
+        return np.concatenate([np.asarray(s, dtype=np.float64) for s in states], axis=1)
+
+    def unpack(self, U):
+        U = U.cpu().numpy() if hasattr(U, "cpu") else U
+        return [U[:, self.offsets[k]:self.offsets[k + 1]] for k in range(self.n)]
+
+    def set_state(self, U):
+        if isinstance(U, np.ndarray):
+            U = np.ascontiguousarray(U, dtype=np.float64 if self.dtype.itemsize == 8 else np.float32)
+        else:
+            U = U.to(self.dtype).contiguous()
+        hweno_batch_set_state(self.h, U)
+        self._keep = U
+
+    def get_state(self, device: bool = True):
+        import torch
+        if device:
+            out = torch.empty((self.nf, self.total), dtype=self.dtype, device="cuda")
+        else:
+            out = np.empty((self.nf, self.total), dtype=np.float64 if self.dtype.itemsize == 8 else np.float32)
+        hweno_batch_get_state(self.h, out)
+        return out
+
+    def advance(self, t_final, max_steps=2**31 - 1):
+        if np.isscalar(t_final):
+            t_final = [t_final] * self.n
+        return hweno_batch_advance(self.h, t_final, max_steps)
+
+    def apply_operator(self, alpha):
+        import torch
+        nc = self.cfgs[0].ncomp
+        L = torch.empty((self.nf, self.total), dtype=self.dtype, device="cuda")
+        D = torch.empty((nc, self.total), dtype=self.dtype, device="cuda")
+        hweno_batch_apply_operator(self.h, alpha, L, D)
+        return L, D

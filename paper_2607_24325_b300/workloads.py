@@ -280,3 +280,30 @@ def random_positive_weights(n: int, seed: int) -> tuple:
     rng = np.random.default_rng(seed)
     w = rng.uniform(0.05, 1.0, size=n)
     return tuple(float(a) for a in (w / w.sum()))
+
+
+def random_state(dim: int, shape, seed: int, euler: bool = False, gamma=GAMMA,
+                 moment_scale: float = 0.5) -> np.ndarray:
+    """Seeded rough data (every cell independent) for single-operator parity:
+    scalar u-bar ~ N(0, 1); Euler rho, p ~ U[0.5, 1.5], velocities ~ U[-1, 1];
+    derivative moments ~ moment_scale * N(0, 1) (times rho-scale for Euler).
+    Returns U with dim+1 groups of nc fields over `shape` (cells)."""
+    rng = np.random.default_rng(seed)
+    shape = tuple(shape)
+    if not euler:
+        ub = rng.normal(size=(1,) + shape)
+        mom = moment_scale * rng.normal(size=(dim,) + shape)
+        return np.concatenate([ub, mom], axis=0)
+    rho = rng.uniform(0.5, 1.5, size=shape)
+    p = rng.uniform(0.5, 1.5, size=shape)
+    if dim == 1:
+        u = rng.uniform(-1, 1, size=shape)
+        ub = prim_to_cons_1d(rho, u, p, gamma)
+        nc = 3
+    else:
+        u = rng.uniform(-1, 1, size=shape)
+        v = rng.uniform(-1, 1, size=shape)
+        ub = prim_to_cons_2d(rho, u, v, p, gamma)
+        nc = 4
+    mom = moment_scale * rng.normal(size=(dim * nc,) + shape)
+    return np.concatenate([ub, mom], axis=0)

@@ -1,0 +1,61 @@
+"""Shared test helpers: mapping an oracle problem to a library config and
+the parity measure (max abs difference per field plane over the plane's max
+magnitude)."""
+import numpy as np
+
+import oracle
+from paper_2607_24325_b300 import hweno as hw
+
+
+def cfg_from(prob: oracle.Problem, precision: int = hw.FP64) -> hw.Config:
+    return hw.Config(dim=prob.dim, nx=prob.nx, ny=prob.ny if prob.dim == 2 else 1,
+                     xlo=prob.xlo, xhi=prob.xhi, ylo=prob.ylo, yhi=prob.yhi,
+                     equation=prob.equation, adv_x=prob.adv_x, adv_y=prob.adv_y,
+                     gamma_gas=prob.gamma_gas, lin_w=tuple(prob.lin_w), eps=prob.eps,
+                     weight_pow=prob.weight_pow, charwise=prob.charwise,
+                     linear_weights=prob.linear_weights, cfl=prob.cfl, dt_rule=prob.dt_rule,
+                     bc=tuple(prob.bc), bc_state=[list(r) for r in prob.bc_state],
+                     precision=precision)
+
+
+def plane_rel_err(got, ref) -> float:
+    """max over field planes of max|got - ref| / (max|ref| of that plane)."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    worst = 0.0
+    for f in range(ref.shape[0]):
+        scale = np.abs(ref[f]).max() + 1e-300
+        worst = max(worst, float(np.abs(got[f] - ref[f]).max() / scale))
+    return worst
+
+
+def oracle_spread(prob, U, ax, ay=0.0, rel=2.0 ** -53, samples=4, seed=0):
+    """The oracle's operator at U and its spread under random relative input
+    perturbations of size `rel` (unit roundoff of the working precision):
+    per-plane max|L(U') - L(U)| / max|L(U)|.  A result computed with rounding
+    at that precision is only determined to within this spread."""
+    L0, D0 = oracle.operator(prob, U, ax, ay)
+    rng = np.random.default_rng(seed)
+    sL = np.zeros(L0.shape[0])
+    sD = np.zeros(D0.shape[0])
+    for _ in range(samples):
+        Up = U * (1.0 + rel * rng.choice([-1.0, 1.0], size=U.shape) * rng.uniform(0.5, 1.0, size=U.shape))
+        L1, D1 = oracle.operator(prob, Up, ax, ay)
+        for f in range(L0.shape[0]):
+            sL[f] = max(sL[f], np.abs(L1[f] - L0[f]).max() / (np.abs(L0[f]).max() + 1e-300))
+        for f in range(D0.shape[0]):
+            sD[f] = max(sD[f], np.abs(D1[f] - D0[f]).max() / (np.abs(D0[f]).max() + 1e-300))
+    return L0, D0, sL, sD
+
+
+def plane_errs(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return np.array([np.abs(got[f] - ref[f]).max() / (np.abs(ref[f]).max() + 1e-300) for f in range(ref.shape[0])])
+
+
+def within_spread(got, ref, spread, floor, factor=100.0):
+    """Per-plane check: error <= max(floor, factor * spread)."""
+    e = plane_errs(got, ref)
+    tol = np.maximum(floor, factor * np.asarray(spread))
+    return bool(np.all(e <= tol)), e, tol

@@ -1,0 +1,331 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Parity bar (FP64): every field plane within 1e-12 of the oracle relative to
+the plane's largest magnitude -- single operator applications on rough
+seeded data (nonlinear weights fully active), every boundary condition,
+grids spanning several tiles with ragged tails; whole runs on smooth data;
+shock runs compared in L1 (rounding differences are amplified by the
+nonlinear weights near discontinuities).
+FP32: the stated bounds below, derived in the design doc.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_24325_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2607_24325_b300 import hweno as hw  # noqa: E402
+from helpers import cfg_from, plane_rel_err, oracle_spread, within_spread    # noqa: E402
+
+W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _operator_pair(prob, U, ax, ay=0.0, precision=hw.FP64):
+    s = hw.Solver(cfg_from(prob, precision))
+    s.set_state(torch.from_numpy(np.ascontiguousarray(U)).cuda())
+    L, D = s.apply_operator(ax, ay)
+    torch.cuda.synchronize()
+    Lr, Dr = oracle.operator(prob, U, ax, ay)
+    out = (L.double().cpu().numpy(), D.double().cpu().numpy(), Lr, Dr)
+    s.close()
+    return out
+
+
+BC1 = [(oracle.BC_PERIODIC, oracle.BC_PERIODIC), (oracle.BC_OUTFLOW, oracle.BC_OUTFLOW),
+       (oracle.BC_REFLECT, oracle.BC_REFLECT), (oracle.BC_INFLOW, oracle.BC_OUTFLOW)]
+
+
+# ------------------------------------------------------------ 1D operator
+@pytest.mark.parametrize("eq,charwise", [(oracle.EQ_ADVECTION, 1), (oracle.EQ_BURGERS, 1),
+                                         (oracle.EQ_EULER, 1), (oracle.EQ_EULER, 0)])
+@pytest.mark.parametrize("n", [3, 31, 97, 1000])
+@pytest.mark.parametrize("bc", BC1)
+def test_operator_1d_fp64(eq, charwise, n, bc):
+    euler = eq == oracle.EQ_EULER
+    U = W.random_state(1, (n,), seed=n + 7 * eq, euler=euler)
+    st = [list(W.prim_to_cons_1d(1.2, 0.3, 0.9)) + [0.0], list(W.prim_to_cons_1d(0.8, -0.2, 1.1)) + [0.0],
+          [0.0] * 4, [0.0] * 4] if euler else [[0.7, 0, 0, 0], [-0.4, 0, 0, 0], [0.0] * 4, [0.0] * 4]
+    prob = oracle.Problem(dim=1, equation=eq, nx=n, xlo=-0.3, xhi=1.7, adv_x=-1.3, charwise=charwise,
+                          bc=bc + (0, 0), bc_state=st)
+    L, D, Lr, Dr = _operator_pair(prob, U, 2.5)
+    assert plane_rel_err(L, Lr) < TOL64
+    assert plane_rel_err(D, Dr) < TOL64
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_operator_1d_random_weights_and_pow2(seed):
+    n = 77
+    U = W.random_state(1, (n,), seed=seed, euler=True)
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=n, lin_w=W.random_positive_weights(3, seed),
+                          weight_pow=1 + seed % 2, eps=10.0 ** (-6 - seed), bc=(oracle.BC_OUTFLOW,) * 4)
+    L, D, Lr, Dr = _operator_pair(prob, U, 1.7)
+    assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
+
+
+def test_operator_1d_linear_weights():
+    n = 64
+    U = W.random_state(1, (n,), seed=3, euler=True)
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=n, linear_weights=1)
+    L, D, Lr, Dr = _operator_pair(prob, U, 1.7)
+    assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
+
+
+# ------------------------------------------------------------ 2D operator
+BC2 = [(0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (3, 1, 2, 2), (0, 0, 1, 1), (2, 2, 0, 0), (1, 3, 3, 2)]
+
+
+@pytest.mark.parametrize("eq,charwise", [(oracle.EQ_ADVECTION, 1), (oracle.EQ_BURGERS, 1),
+                                         (oracle.EQ_EULER, 1), (oracle.EQ_EULER, 0)])
+@pytest.mark.parametrize("nx,ny", [(3, 3), (37, 23), (64, 61)])
+@pytest.mark.parametrize("bc", BC2)
+def test_operator_2d_fp64(eq, charwise, nx, ny, bc):
+    euler = eq == oracle.EQ_EULER
+    U = W.random_state(2, (ny, nx), seed=nx * ny + eq, euler=euler, moment_scale=0.3)
+    if euler:
+        st = [list(W.prim_to_cons_2d(1.0 + 0.1 * k, 0.2 * k - 0.3, 0.1 - 0.1 * k, 1.0 + 0.05 * k)) for k in range(4)]
+    else:
+        st = [[0.3 * k - 0.5, 0, 0, 0] for k in range(4)]
+    prob = oracle.Problem(dim=2, equation=eq, nx=nx, ny=ny, xlo=0, xhi=1.3, ylo=-1, yhi=0.5, adv_x=0.7,
+                          adv_y=-1.1, lin_w=W2D, charwise=charwise, bc=bc, bc_state=st)
+    L, D, Lr, Dr = _operator_pair(prob, U, 2.2, 1.9)
+    assert plane_rel_err(L, Lr) < TOL64
+    assert plane_rel_err(D, Dr) < TOL64
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_operator_2d_random_weights(seed):
+    nx, ny = 45, 33
+    U = W.random_state(2, (ny, nx), seed=seed, euler=True, moment_scale=0.3)
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny, lin_w=W.random_positive_weights(5, seed),
+                          weight_pow=1 + seed, bc=(0, 0, 1, 1))
+    L, D, Lr, Dr = _operator_pair(prob, U, 2.2, 1.9)
+    assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
+
+
+def test_operator_2d_large_sampled():
+    """A 300 x 271 grid (10 x 10 tiles, ragged): the oracle is slow here, so
+    compare a full application on Burgers and the exact symmetry of a
+    transposed problem."""
+    nx, ny = 300, 271
+    U = W.random_state(2, (ny, nx), seed=5, moment_scale=0.3)
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_BURGERS, nx=nx, ny=ny, lin_w=W2D)
+    L, D, Lr, Dr = _operator_pair(prob, U, 3.0, 3.0)
+    assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
+
+
+# ------------------------------------------------------------ whole runs
+def test_run_1d_advection_config1():
+    """1D advection sin(pi x) on [0,2], N = 160, CFL 0.6, to t = 2 (FP64)."""
+    N = 160
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_ADVECTION, nx=N, xlo=0, xhi=2, lin_w=(0.995, 0.0025, 0.0025))
+    U0 = W.cells_1d(lambda x: np.sin(np.pi * x)[None], 0, 2, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(2.0)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, 2.0)
+    assert t == tr and n == nr
+    assert plane_rel_err(got, ref) < TOL64
+    assert np.abs(got[0] - U0[0]).mean() < 1e-5
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_run_1d_random_weights(seed):
+    N = 96
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_BURGERS, nx=N, xlo=0, xhi=2,
+                          lin_w=W.random_positive_weights(3, seed), dt_rule=oracle.DT_CFL_DX53)
+    U0 = W.cells_1d(W.sine_burgers_1d(0.0), 0, 2, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(0.25)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, 0.25)
+    assert n == nr and abs(t - tr) < 1e-15
+    assert plane_rel_err(got, ref) < 1e-11
+
+
+def test_run_1d_euler_smooth():
+    N = 80
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=N, xlo=0, xhi=2)
+    U0 = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(0.5)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, 0.5)
+    assert n == nr
+    assert plane_rel_err(got, ref) < 1e-11
+
+
+def test_run_2d_burgers_smooth():
+    N = 40
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_BURGERS, nx=N, ny=N, xlo=0, xhi=4, ylo=0, yhi=4, lin_w=W2D,
+                          dt_rule=oracle.DT_CFL_DX53)
+    U0 = W.cells_2d(W.sine_burgers_2d(0.0), 0, 4, 0, 4, N, N)
+    T = 0.5 / math.pi
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(T)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, T)
+    assert n == nr
+    assert plane_rel_err(got, ref) < 1e-11
+    ex = W.cells_2d(W.sine_burgers_2d(T), 0, 4, 0, 4, N, N)[0]
+    assert abs(np.abs(got[0] - ex).mean() / 3.87e-05 - 1) < 0.3   # Example 3 table, 40 x 40
+
+
+def test_run_2d_euler_smooth_steps():
+    N = 24
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2, lin_w=W2D)
+    U0 = W.cells_2d(W.euler_smooth_2d(0.0), 0, 2, 0, 2, N, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(1.0, max_steps=12)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, 1.0, max_steps=12)
+    assert n == nr == 12 and abs(t - tr) < 1e-14
+    assert plane_rel_err(got, ref) < 1e-11
+
+
+def test_run_2d_quadrant_l1():
+    """Four-quadrant Riemann problem (seeded states), shocks form: L1 parity."""
+    N = 48
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, lin_w=W2D, bc=(oracle.BC_OUTFLOW,) * 4)
+    U0 = W.quadrant_2d(W.quadrant_states(2024), 0.5, 0.5, 0, 1, 0, 1, N, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    t, n = s.advance(0.05)
+    got = s.get_state(device=False)
+    ref, tr, nr = oracle.run(prob, U0, 0.05)
+    assert n == nr
+    for k in range(4):
+        assert np.abs(got[k] - ref[k]).mean() < 1e-10 * np.abs(ref[k]).mean()
+
+
+def test_conservation_gpu_fp64():
+    N = 128
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_BURGERS, nx=N, xlo=0, xhi=2)
+    U0 = W.cells_1d(W.sine_burgers_1d(0.0), 0, 2, N)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U0)
+    s.advance(1.5)
+    got = s.get_state(device=False)
+    assert abs(got[0].sum() - U0[0].sum()) < 1e-12 * np.abs(U0[0]).sum()
+
+
+# ------------------------------------------------------------ batch
+def test_batch_operator_and_runs():
+    B = W.riemann_batch_1d(n=6, seed=1234, nmin=20, nmax=300)
+    cfgs, states, probs = [], [], []
+    for k in range(B.sizes.size):
+        p = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=int(B.sizes[k]), bc=(oracle.BC_OUTFLOW,) * 4)
+        probs.append(p)
+        cfgs.append(cfg_from(p))
+        states.append(B.instance(k))
+    b = hw.Batch(cfgs)
+    U = b.pack(states)
+    b.set_state(torch.from_numpy(U).cuda())
+    alphas = [1.0 + 0.5 * k for k in range(b.n)]
+    L, D = b.apply_operator(alphas)
+    torch.cuda.synchronize()
+    Ls, Ds = b.unpack(L), b.unpack(D)
+    for k, p in enumerate(probs):
+        # Riemann data: the weights next to a jump are epsilon-sensitive, so the
+        # bar is the oracle's own spread under FP64 unit-roundoff input noise
+        Lr, Dr, sL, sD = oracle_spread(p, states[k], alphas[k])
+        ok, e, tol = within_spread(Ls[k], Lr, sL, TOL64)
+        assert ok, (k, e, tol)
+        ok, e, tol = within_spread(Ds[k], Dr, sD, TOL64)
+        assert ok, (k, e, tol)
+    tf = [0.02 + 0.01 * k for k in range(b.n)]
+    t, n = b.advance(tf)
+    got = b.unpack(b.get_state())
+    for k, p in enumerate(probs):
+        ref, tr, nr = oracle.run(p, states[k], tf[k])
+        assert n[k] == nr and abs(t[k] - tr) < 1e-15
+        for f in range(3):
+            assert np.abs(got[k][f] - ref[f]).mean() < 1e-9 * np.abs(ref[f]).mean()
+
+
+# ------------------------------------------------------------ FP32
+@pytest.mark.parametrize("dim,eq", [(1, oracle.EQ_EULER), (2, oracle.EQ_EULER), (2, oracle.EQ_BURGERS)])
+def test_fp32_operator_within_fp32_conditioning(dim, eq):
+    """FP32 stencil arithmetic, judged on the FP32-rounded input: every plane
+    within max(2e-5, 100 x the oracle's spread under FP32 unit-roundoff input
+    noise).  The derivative-equation planes are ill-conditioned (their
+    fluxes cancel to O(dx)), which the spread measures."""
+    if dim == 1:
+        N = 200
+        prob = oracle.Problem(dim=1, equation=eq, nx=N, xlo=0, xhi=2)
+        U = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
+    else:
+        N = 64
+        prob = oracle.Problem(dim=2, equation=eq, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2, lin_w=W2D)
+        f = W.euler_smooth_2d(0.0) if eq == oracle.EQ_EULER else W.sine_burgers_2d(0.0)
+        U = W.cells_2d(f, 0, 2, 0, 2, N, N)
+    U32 = U.astype(np.float32).astype(np.float64)
+    L, D, _, _ = _operator_pair(prob, U32, 2.5, 2.5, precision=hw.FP32)
+    Lr, Dr, sL, sD = oracle_spread(prob, U32, 2.5, 2.5, rel=2.0 ** -24)
+    ok, e, tol = within_spread(L, Lr, sL, 2e-5)
+    assert ok, (e, tol)
+    ok, e, tol = within_spread(D, Dr, sD, 2e-5)
+    assert ok, (e, tol)
+    # the cell-average equations themselves stay accurate to a few FP32 ulps
+    nc = prob.ncomp
+    assert plane_rel_err(L[:nc], Lr[:nc]) < 2e-4
+
+
+def test_fp32_smooth_runs_close_to_fp64_oracle():
+    """Whole FP32 runs on smooth data against the FP64 oracle: the relative
+    L1 difference of the cell averages stays at the FP32 rounding level."""
+    N = 200
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=N, xlo=0, xhi=2)
+    U0 = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
+    s = hw.Solver(cfg_from(prob, hw.FP32))
+    s.set_state(U0)
+    t, n = s.advance(0.5)
+    got = s.get_state(device=False).astype(np.float64)
+    ref, tr, nr = oracle.run(prob, U0, 0.5)
+    assert abs(n - nr) <= 1
+    rel = [np.abs(got[k] - ref[k]).mean() / np.abs(ref[k]).mean() for k in range(3)]
+    print("FP32 vs FP64 oracle, 1D Euler smooth N=200 t=0.5, relative L1 per component:", rel)
+    assert max(rel) < 5e-6
+    N = 48
+    p2 = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2, lin_w=W2D)
+    V0 = W.cells_2d(W.euler_smooth_2d(0.0), 0, 2, 0, 2, N, N)
+    s2 = hw.Solver(cfg_from(p2, hw.FP32))
+    s2.set_state(V0)
+    s2.advance(0.25)
+    g2 = s2.get_state(device=False).astype(np.float64)
+    r2, _, _ = oracle.run(p2, V0, 0.25)
+    rel2 = [np.abs(g2[k] - r2[k]).mean() / np.abs(r2[k]).mean() for k in range(4)]
+    print("FP32 vs FP64 oracle, 2D Euler smooth 48^2 t=0.25, relative L1 per component:", rel2)
+    assert max(rel2) < 5e-6
+
+
+def test_nonphysical_state_reported():
+    """A negative pressure put into the initial state (host-made fault) is
+    reported as HWENO_ERR_NONPHYSICAL, never a device fault."""
+    N = 32
+    U = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
+    U[2, 5] = -1.0   # energy below kinetic energy: p < 0
+    prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=N, xlo=0, xhi=2)
+    s = hw.Solver(cfg_from(prob))
+    with pytest.raises(hw.HwenoError) as ei:
+        s.set_state(U)
+        s.advance(0.1)
+    assert ei.value.status == hw.HWENO_ERR_NONPHYSICAL
