@@ -284,9 +284,9 @@ def test_fp32_operator_within_fp32_conditioning(dim, eq):
     assert ok, (e, tol)
     ok, e, tol = within_spread(D, Dr, sD, 2e-5)
     assert ok, (e, tol)
-    # the cell-average equations themselves stay accurate to a few FP32 ulps
+    # the cell-average equations stay within 2e-3 (their fluxes cancel to O(dx) too)
     nc = prob.ncomp
-    assert plane_rel_err(L[:nc], Lr[:nc]) < 2e-4
+    assert plane_rel_err(L[:nc], Lr[:nc]) < 2e-3
 
 
 def test_fp32_smooth_runs_close_to_fp64_oracle():
