@@ -37,8 +37,13 @@ W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
 # Algorithmic flops of one cell update in one stage, counted from the
 # executed FP instructions of the stage kernel (ncu sass op counters, see
 # profiles/) with the ring-cell redundancy of the two passes removed.
-FLOPS_PER_CELL_STAGE = {"fp64": 7000.0, "fp32": 7000.0}
-FLOPS_SOURCE = "estimate (operation count of the method); replaced by counted flops once profiled"
+FLOPS_PER_CELL_STAGE = {"fp64": 6476.0, "fp32": 6054.0}
+FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the stage kernel at 1536^2, ring-lane "
+                "redundancy removed (profiles/stage2d_euler_char_fp*_1536.md)")
+# DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
+# the bench grid by cell count; None once the kernel has changed since the capture.
+TRAFFIC_PER_CELL = {"fp64": 647.04e6 / 1536 ** 2, "fp32": 309.01e6 / 1536 ** 2}
+TRAFFIC_NOTE = "stage-1 launch at 1536^2 scaled by cells (stage 1 reads 12 and writes 20 planes)"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)
 # and write F; F = 12 stored fields, D = 8 limited derivatives -> (8F+D)/3 words.
@@ -312,8 +317,10 @@ def main():
         key = "fp64" if prec == hw.FP64 else "fp32"
         flops_launch = FLOPS_PER_CELL_STAGE[key] * ncells
         achieved = flops_launch / (r["stage_ms_avg"] * 1e-3) / 1e12
+        traffic = TRAFFIC_PER_CELL.get(key)
         return {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": None,
+                "frac": achieved / peak_tf, "traffic": None if traffic is None else traffic * ncells,
+                "traffic_unit": "bytes per launch", "traffic_note": TRAFFIC_NOTE,
                 "kernel": f"k_stage2d<{'double' if prec == hw.FP64 else 'float'},EULER,char>",
                 "peak_source": "measured FMA probe (hweno_peak_fma) on this GPU",
                 "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[key], "flops_source": FLOPS_SOURCE,
