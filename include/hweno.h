@@ -189,6 +189,32 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,
                                         void* dhat_out);
 
+/* ---- Allocation-free step (the paper has no counterpart: this serves
+ * callers that cannot allocate device memory when they need a step, e.g. a
+ * host that has given the whole device memory budget to its own pool
+ * allocator, or a latency-critical loop that must not pay cudaMalloc's
+ * implicit device synchronisation). ----
+ * One SSP-RK3 step (Sec. 2.1 Step 4) of the single 1D problem described by
+ * cfg (dim must be 1), with the given dt and Lax-Friedrichs constant alpha:
+ * U_out = step(U_in).  U_in and U_out are caller device buffers [2*nc][nx]
+ * of the config's element type (they may be the same buffer); the work is
+ * queued on cuda_stream (cudaStream_t, NULL = legacy default stream) and the
+ * call returns without synchronising.
+ * No memory is allocated: the two intermediate stage states, the stage-1
+ * limited derivatives, the control block and the task table live in a
+ * 16 MiB file-scope device array that every GPU which loads the library
+ * holds until exit.  That caps nx at about 139,000 cells for FP64 Euler
+ * (about 419,000 for FP64 scalar equations, twice these in FP32); larger nx
+ * is rejected with HWENO_ERR_ARG and a message giving the limit.
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array, so calls whose work overlaps on
+ * the GPU (different streams, or threads without ordering) race and corrupt
+ * each other's results; order them on one stream.
+ * Errors: HWENO_ERR_ARG (config, pointers, dt/alpha, size), HWENO_ERR_CUDA. */
+hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const void* U_in, void* U_out, double dt,
+                                   double alpha, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,13 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
 
 }  // namespace
 
+namespace hw {
+// Error reporting and config validation for entry points defined in other
+// translation units (the allocation-free step).
+hweno_status report_error(hweno_status st, const char* msg) { return fail(st, "%s", msg); }
+hweno_status check_config(const hweno_config* cfg, int expect_dim) { return validate(cfg, expect_dim); }
+}  // namespace hw
+
 // One engine serves both a single grid (n_inst = 1) and a 1D batch.
 struct Engine {
   hweno_config cfg{};

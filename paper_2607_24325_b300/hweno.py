@@ -32,7 +32,7 @@ EXPORTS = (
     "hweno_step", "hweno_advance", "hweno_set_profiling", "hweno_profile", "hweno_peak_fma",
     "hweno_batch_create", "hweno_batch_destroy",
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
-    "hweno_batch_advance", "hweno_batch_apply_operator",
+    "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
 )
 
 
@@ -147,6 +147,7 @@ def load():
     L.hweno_batch_advance.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int)]
     L.hweno_batch_apply_operator.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
+    L.hweno_step_1d_noalloc.argtypes = [cp, vp, vp, C.c_double, C.c_double, vp]
     _lib = L
     return L
 
@@ -291,6 +292,17 @@ def hweno_batch_apply_operator(h, alpha, L_out, dhat_out):
     pl, _ = _buf(L_out)
     pd, _ = _buf(dhat_out)
     _check(load().hweno_batch_apply_operator(h, a, C.c_void_p(pl), C.c_void_p(pd)))
+
+
+def hweno_step_1d_noalloc(cfg: Config, U_in, U_out, dt, alpha, stream=None):
+    """One SSP-RK3 step of a 1D problem without any device allocation (its
+    working memory is a fixed 16 MiB device array inside the library); for
+    callers that cannot allocate device memory.  U_in, U_out: CUDA tensors."""
+    c = cfg.to_c()
+    pi, _ = _buf(U_in)
+    po, _ = _buf(U_out)
+    _check(load().hweno_step_1d_noalloc(C.byref(c), C.c_void_p(pi), C.c_void_p(po), dt, alpha,
+                                        stream if stream is not None else _current_stream()))
 
 
 # ---- conveniences ----
