@@ -37,13 +37,14 @@ W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
 # Algorithmic flops of one cell update in one stage, counted from the
 # executed FP instructions of the stage kernel (ncu sass op counters, see
 # profiles/) with the ring-cell redundancy of the two passes removed.
-FLOPS_PER_CELL_STAGE = {"fp64": 6476.0, "fp32": 6054.0}
-FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the stage kernel at 1536^2, ring-lane "
-                "redundancy removed (profiles/stage2d_euler_char_fp*_1536.md)")
+FLOPS_PER_CELL_STAGE = {"fp64": 5842.0, "fp32": 5466.0, "fp32_ind64": 1889.0}
+FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
+                "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); the "
+                "mixed kernel counts its FP64 flops (its bound)")
 # DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
 # the bench grid by cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 647.04e6 / 1536 ** 2, "fp32": 309.01e6 / 1536 ** 2}
-TRAFFIC_NOTE = "stage-1 launch at 1536^2 scaled by cells (stage 1 reads 12 and writes 20 planes)"
+TRAFFIC_PER_CELL = {"fp64": 661.6e6 / 1536 ** 2, "fp32": 348.4e6 / 1536 ** 2, "fp32_ind64": 322.6e6 / 1536 ** 2}
+TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 1536^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)
 # and write F; F = 12 stored fields, D = 8 limited derivatives -> (8F+D)/3 words.
@@ -197,12 +198,15 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_precision(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, stream_ctx=None):
-    """Advance `steps` steps of the workload at `precision`; returns timings."""
+def time_arm(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, theta=None):
+    """Advance `steps` steps of the workload at `precision` (optionally with
+    the learned indicator); returns timings and the final density."""
     n = GRID["n"]
     cfg = hw.Config(dim=2, nx=n, ny=n, equation=hw.EQ_EULER, lin_w=W2D, bc=(hw.BC_OUTFLOW,) * 4,
                     precision=precision)
     s = hw.Solver(cfg)
+    if theta is not None:
+        hw.hweno_indicator_load(s.h, theta, 0.5)
     s.set_state(U0_dev)
     s.advance(1e30, max_steps=warmup)
     s.set_state(U0_dev)       # the timed steps start from the workload's initial state
@@ -214,16 +218,52 @@ def time_precision(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, str
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(sampler_gpu) as clk:
         ev0.record(stream)
-        t, n = s.advance(1e30, max_steps=steps)
+        t, nsteps = s.advance(1e30, max_steps=steps)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     stage_ms, stage_n, launches = s.profile()
     s.set_profiling(False)
-    assert n == steps, (n, steps)
-    out = {"ms": ms, "stage_ms_avg": stage_ms / max(stage_n, 1), "stage_launches": stage_n,
-           "launches": launches, "clocks": clk.summary(), "solver": s}
-    return out
+    assert nsteps == steps, (nsteps, steps)
+    rho = s.get_state()[0].double().clone()
+    smooth = None
+    if theta is not None:
+        sm = torch.empty((n * n,), dtype=torch.uint8, device="cuda")
+        hw.hweno_indicator_mask(s.h, sm, None)
+        smooth = float(sm.float().mean().item())
+    s.close()
+    return {"ms": ms, "stage_ms_avg": stage_ms / max(stage_n, 1), "stage_launches": stage_n,
+            "launches": launches, "clocks": clk.summary(), "rho": rho, "t": t, "smooth_fraction": smooth}
+
+
+def train_indicator(verbose=False):
+    """The learned indicator for the bench: trained on the GPU (outside the
+    timed region) on shock / entropy-wave snapshots and on four-quadrant
+    problems with other seeds than the bench's."""
+    import torch
+    from paper_2607_24325_b300 import hweno as hw
+    from paper_2607_24325_b300 import indicator as IND
+    from paper_2607_24325_b300 import workloads as W
+    data = IND.generate(seeds=[1, 2, 3], n=160, times=(0.0, 0.03, 0.06, 0.1))
+    feats, devs = [data.feat], [data.dev]
+    for seed in (7, 8, 9):
+        n = 192
+        cfg = hw.Config(dim=2, nx=n, ny=n, equation=hw.EQ_EULER, lin_w=W2D, bc=(hw.BC_OUTFLOW,) * 4)
+        s = hw.Solver(cfg)
+        s.set_state(torch.from_numpy(W.quadrant_2d(W.quadrant_states(seed), 0.5, 0.5, 0, 1, 0, 1, n, n)).cuda())
+        for t in (0.0, 0.05, 0.1):
+            if t > 0:
+                s.advance(t)
+            F = torch.empty((n * n, 75), dtype=torch.float32, device="cuda")
+            D = torch.empty((n * n,), dtype=torch.float32, device="cuda")
+            hw.hweno_indicator_features(s.h, F)
+            hw.hweno_indicator_labels(s.h, D)
+            feats.append(F)
+            devs.append(D)
+        s.close()
+    full = IND.Dataset(feat=torch.cat(feats), dev=torch.cat(devs), n=sum(f.shape[0] for f in feats))
+    theta, losses = IND.train(full, epochs=6, seed=0, verbose=verbose)
+    return theta, IND.evaluate(theta, full), losses
 
 
 def e2e_run(hw, torch, U0_host_pinned, precision, steps):
@@ -249,6 +289,49 @@ def e2e_run(hw, torch, U0_host_pinned, precision, steps):
     return el, nbytes, out
 
 
+def run_batch1d(args, hw, torch, rank, local):
+    """256 1D Euler Riemann problems (seed 1234, sizes log-uniform in
+    [256, 8192], transmissive, characteristic-wise), one launch per stage for
+    all instances.  The batch (~28 MB in FP64) fits in L2, so L2 is flushed
+    (256 MB write) before every timed step and each step is timed alone."""
+    from paper_2607_24325_b300 import workloads as W
+    torch.cuda.set_device(local)
+    B = W.riemann_batch_1d(n=256, seed=1234)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, prec in (("fp64", hw.FP64), ("fp32", hw.FP32)):
+        cfgs = [hw.Config(dim=1, nx=int(B.sizes[k]), equation=hw.EQ_EULER, bc=(hw.BC_OUTFLOW,) * 4, precision=prec)
+                for k in range(B.sizes.size)]
+        b = hw.Batch(cfgs)
+        U = torch.from_numpy(b.pack([B.instance(k) for k in range(b.n)])).cuda()
+        b.set_state(U)
+        b.advance(1e30, max_steps=args.warmup)
+        b.set_state(U)
+        stream = torch.cuda.ExternalStream(b.stream)
+        total_ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.advance(1e30, max_steps=1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        out[name] = {"value": b.total * 3 * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
+                     "cells": int(b.total)}
+        b.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["fp64"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seed 1234)",
+                "config": {"workload": "256 1D Euler Riemann problems, sizes log-uniform 256-8192, one launch "
+                                       "per stage", "cells": out["fp64"]["cells"],
+                           "l2": "flushed (256 MB write) before every timed step"},
+                "arms": out}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -257,8 +340,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N_GRID, help="cells per side (profiling runs use a small grid)")
-    ap.add_argument("--only", choices=["fp64", "fp32"], default=None, help="time one precision only")
+    ap.add_argument("--only", choices=["fp64", "fp32", "fp32_ind64", "fp32_learned", "fp32_ind64_learned"],
+                    default=None, help="time one arm only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["euler2d_quadrant", "batch1d"], default="euler2d_quadrant",
+                    help="batch1d: 256 seeded 1D Euler Riemann problems of uneven sizes in one batch")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -270,6 +356,9 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2607_24325_b300 import hweno as hw
+    if args.workload == "batch1d":
+        run_batch1d(args, hw, torch, rank, local)
+        return
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -282,24 +371,35 @@ def main():
     U0_pin = U0_t.pin_memory()
     U0_dev = U0_pin.cuda()
 
-    # headline: FP64 plain (nonlinear, characteristic-wise) path; FP32 beside it
-    r64 = r32 = None
-    if args.only in (None, "fp64"):
-        r64 = time_precision(hw, torch, U0_dev, hw.FP64, args.steps, args.warmup, local)
-    if args.only in (None, "fp32"):
-        r32 = time_precision(hw, torch, U0_dev, hw.FP32, args.steps, args.warmup, local)
-    head = r64 if r64 is not None else r32
+    # arms: FP64 plain (the reference), FP32, FP32 with FP64 smoothness
+    # indicators and weights (the headline), and both FP32 forms with the
+    # learned troubled-cell indicator
+    plan = [("fp64", hw.FP64, False), ("fp32", hw.FP32, False), ("fp32_ind64", hw.FP32_IND64, False),
+            ("fp32_learned", hw.FP32, True), ("fp32_ind64_learned", hw.FP32_IND64, True)]
+    if args.only is not None:
+        plan = [p for p in plan if p[0] == args.only]
+    theta = ind_eval = None
+    if any(learned for _, _, learned in plan):
+        theta, ind_eval, _ = train_indicator()
+    arms = {}
+    for name, prec, learned in plan:
+        arms[name] = time_arm(hw, torch, U0_dev, prec, args.steps, args.warmup, local,
+                              theta=theta if learned else None)
+        arms[name]["precision"] = prec
+    head_name = "fp32_ind64" if "fp32_ind64" in arms else next(iter(arms))
+    head = arms[head_name]
     ms_head = head["ms"]
     if world > 1:
         x = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
         dist.all_reduce(x, op=dist.ReduceOp.MAX)
         ms_head = float(x.item())
     value = world * ncells * 3 * args.steps / (ms_head * 1e-3)
+    ref_rho = arms["fp64"]["rho"] if "fp64" in arms else None
 
     # end to end with host buffers
     e2e = None
     if not args.no_e2e:
-        prec = hw.FP64 if r64 is not None else hw.FP32
+        prec = head["precision"]
         src = U0_pin if prec == hw.FP64 else U0_t.float().pin_memory()
         e2e_s, nbytes, _ = e2e_run(hw, torch, src, prec, args.steps)
         e2e = {"value": world * ncells * 3 * args.steps / e2e_s, "unit": UNIT,
@@ -313,18 +413,27 @@ def main():
     fp64_peak = hw.hweno_peak_fma(hw.FP64) / 1e12
     fp32_peak = hw.hweno_peak_fma(hw.FP32) / 1e12
 
-    def roofline(r, prec, peak_tf):
-        key = "fp64" if prec == hw.FP64 else "fp32"
-        flops_launch = FLOPS_PER_CELL_STAGE[key] * ncells
-        achieved = flops_launch / (r["stage_ms_avg"] * 1e-3) / 1e12
+    def roofline(r, prec, peak_tf, learned=False):
+        key = "fp64" if prec == hw.FP64 else ("fp32_ind64" if prec == hw.FP32_IND64 else "fp32")
+        if learned:
+            key = key + "_learned"
+        fl = FLOPS_PER_CELL_STAGE.get(key)
         traffic = TRAFFIC_PER_CELL.get(key)
-        return {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                "frac": achieved / peak_tf, "traffic": None if traffic is None else traffic * ncells,
-                "traffic_unit": "bytes per launch", "traffic_note": TRAFFIC_NOTE,
-                "kernel": f"k_stage2d<{'double' if prec == hw.FP64 else 'float'},EULER,char>",
-                "peak_source": "measured FMA probe (hweno_peak_fma) on this GPU",
-                "flops_per_cell_stage": FLOPS_PER_CELL_STAGE[key], "flops_source": FLOPS_SOURCE,
-                "avg_launch_ms": r["stage_ms_avg"]}
+        out = {"bound": "alu", "peak": peak_tf, "unit": "TFLOP/s",
+               "kernel": f"k_stage2d<{'double' if prec == hw.FP64 else 'float'},EULER,char"
+                         f"{',fp64 weights' if prec == hw.FP32_IND64 else ''}>",
+               "peak_source": "measured FMA probe (hweno_peak_fma) on this GPU",
+               "avg_launch_ms": r["stage_ms_avg"],
+               "traffic": None if traffic is None else traffic * ncells,
+               "traffic_unit": "bytes per launch", "traffic_note": TRAFFIC_NOTE}
+        if fl is not None:
+            achieved = fl * ncells / (r["stage_ms_avg"] * 1e-3) / 1e12
+            out.update({"achieved": achieved, "frac": achieved / peak_tf, "flops_per_cell_stage": fl,
+                        "flops_source": FLOPS_SOURCE})
+        else:
+            out.update({"achieved": None, "frac": None, "flops_per_cell_stage": None,
+                        "flops_source": "not yet counted for this kernel"})
+        return out
 
     def hbm(r, esz):
         bytes_launch = words_per_cell_stage() * esz * ncells
@@ -332,39 +441,51 @@ def main():
         return {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak, "peak_source": hbm_src,
                 "bytes_per_cell_stage": words_per_cell_stage() * esz}
 
+    def arm_summary(name, r):
+        prec = r["precision"]
+        v = world * ncells * 3 * args.steps / (r["ms"] * 1e-3)
+        out = {"value": v, "ms_per_step": r["ms"] / args.steps,
+               "dtype": {hw.FP64: "f64", hw.FP32: "f32", hw.FP32_IND64: "f32 (f64 indicators/weights)"}[prec],
+               "roofline": roofline(r, prec, fp32_peak if prec == hw.FP32 else fp64_peak,
+                                    learned=r["smooth_fraction"] is not None),
+               "hbm": hbm(r, 8 if prec == hw.FP64 else 4), "clocks": r["clocks"], "gpu_launches": r["launches"]}
+        if ref_rho is not None:
+            out["l1_rho_vs_fp64"] = float((r["rho"] - ref_rho).abs().mean() / ref_rho.abs().mean())
+            if "fp64" in arms:
+                out["speedup_vs_fp64"] = arms["fp64"]["ms"] / r["ms"]
+        if r["smooth_fraction"] is not None:
+            out["linear_path_fraction"] = r["smooth_fraction"]
+        return out
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(256)
 
     if rank == 0:
-        head_prec = hw.FP64 if r64 is not None else hw.FP32
+        summ = {k: arm_summary(k, r) for k, r in arms.items()}
+        hs = summ[head_name]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_head / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if r64 is not None else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": hs["dtype"],
             "data": "synthetic (seeded four-quadrant Riemann states, seed 2024)",
-            "config": {"workload": f"2D Euler four-quadrant Riemann {ng}^2, transmissive, "
-                                   f"{'FP64' if r64 is not None else 'FP32'} characteristic-wise nonlinear "
-                                   "HWENO, SSP-RK3",
+            "config": {"workload": f"2D Euler four-quadrant Riemann {ng}^2, transmissive, characteristic-wise "
+                                   f"nonlinear HWENO, SSP-RK3, arm {head_name}",
                        "nx": ng, "ny": ng, "cells": ncells, "stages_per_step": 3,
                        "l2": "inputs larger than L2 (state 1.6 GB FP64, 0.8 GB FP32 at 4096^2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline(head, head_prec, fp64_peak if head_prec == hw.FP64 else fp32_peak),
-            "hbm": hbm(head, 8 if head_prec == hw.FP64 else 4),
+            "roofline": hs["roofline"],
+            "roofline_note": "bound 'alu': FP64 pipe for the fp64 and fp32_ind64 arms, FP32 FMA pipe for fp32; "
+                             "peaks from the FMA probe on this GPU (recipe nominal FP64 1.25 TFLOP/s)",
+            "hbm": hs["hbm"],
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(head["launches"]),
             "clocks": head["clocks"],
+            "arms": summ,
+            "learned_indicator": ind_eval,
         }
-        if r64 is not None and r32 is not None:
-            value32 = world * ncells * 3 * args.steps / (r32["ms"] * 1e-3)
-            line["fp32"] = {"value": value32, "ms_per_step": r32["ms"] / args.steps, "dtype": "f32",
-                            "roofline": roofline(r32, hw.FP32, fp32_peak), "hbm": hbm(r32, 4),
-                            "clocks": r32["clocks"], "speedup_vs_fp64": value32 / value}
         print(json.dumps(line), flush=True)
-    for r in (r64, r32):
-        if r is not None:
-            r["solver"].close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

@@ -23,7 +23,7 @@
  *    (rho, rho u, rho v, E)).  1D v-bar is the mean of u_x over the cell
  *    (Sec. 2.1); 2D v-bar = (1/dy) int u_x dOmega and w-bar = (1/dx) int u_y
  *    dOmega are the scaled moments of Sec. 2.2.
- *  - Element type is double for HWENO_FP64 solvers and float for HWENO_FP32.
+ *  - Element type is double for HWENO_FP64 solvers and float otherwise.
  *  - Pointers flagged on_device are device pointers on the current device;
  *    otherwise host pointers (pinned or pageable).  The caller owns every
  *    buffer it passes; the library owns its internal workspace (stage states,
@@ -58,7 +58,7 @@ typedef enum {
 
 enum { HWENO_EQ_ADVECTION = 0, HWENO_EQ_BURGERS = 1, HWENO_EQ_EULER = 2 };
 enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECT = 2, HWENO_BC_INFLOW = 3 };
-enum { HWENO_FP64 = 0, HWENO_FP32 = 1 };
+enum { HWENO_FP64 = 0, HWENO_FP32 = 1, HWENO_FP32_IND64 = 2 };
 enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
 
 /* Problem statement and scheme parameters.
@@ -81,7 +81,10 @@ enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
  *                 cfl / (alpha_x/hx + alpha_y/hy)
  *  bc[4]          x-low, x-high, y-low, y-high: HWENO_BC_*
  *  bc_state[4][4] conservative state imposed by HWENO_BC_INFLOW sides
- *  precision      HWENO_FP64 or HWENO_FP32 (storage and stencil arithmetic)
+ *  precision      HWENO_FP64, HWENO_FP32 (storage and stencil arithmetic), or
+ *                 HWENO_FP32_IND64 (FP32 storage and stencil arithmetic; the
+ *                 coefficients entering the smoothness indicators, the
+ *                 indicators and the nonlinear weights in FP64)
  */
 typedef struct {
   int dim;
@@ -120,6 +123,18 @@ void hweno_destroy(hweno_solver* s);
 void* hweno_stream(hweno_solver* s);
 /* Number of stored fields nf = nc * (dim + 1) and cells per field. */
 hweno_status hweno_shape(const hweno_solver* s, int* nfields, size_t* ncells);
+
+/* Initial data u0 (Sec. 1, Eq. hyperbolic-conservation-laws): u0 is called
+ * with n points (x[k], y[k]) (y = 0 in 1D) and writes the nc conserved
+ * components of u0 at each point to u[k*nc + c]; ctx is passed through.
+ * Cell averages come from nq x nq (1D: nq) Gauss-Legendre points; the
+ * derivative moments are exact face differences: 1D v-bar = (u0(x_{i+1/2})
+ * - u0(x_{i-1/2})) / dx, 2D v-bar = Gauss mean over y of the x-face
+ * difference (= (1/dy) int u_x), w-bar likewise.  Jumps must lie on faces or
+ * be resolved by the caller.  Then acts as hweno_set_state.  Host code;
+ * nq in [1, 16]. */
+typedef void (*hweno_u0_fn)(int n, const double* x, const double* y, double* u, void* ctx);
+hweno_status hweno_project(hweno_solver* s, hweno_u0_fn u0, void* ctx, int nq);
 
 /* Copy a state in (U[nf][ny][nx]) and compute its wave speeds; resets t. */
 hweno_status hweno_set_state(hweno_solver* s, const void* U, int on_device);
@@ -188,6 +203,59 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
  * L_out [nf][total], dhat_out [nc][total] (device buffers). */
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,
                                         void* dhat_out);
+
+/* ---- Learned troubled-cell indicator (no counterpart in the paper; it
+ * decides which cells may use the linear reconstruction p0, omega = gamma of
+ * Eq. rewrite-2D, while the full nonlinear characteristic HWENO path stays
+ * the fallback).  2D solvers only. ----
+ * Features of a cell: the 5x5 patch (offsets -2..2, ghost cells by the
+ * solver's boundary rules) of the density's u-bar, v-bar, w-bar, scaled by
+ * s = 1/(range of the patch's u-bar + 1e-3 |centre u-bar| + 1e-30), the
+ * centre value subtracted from the u-bar entries; 75 floats ordered
+ * [field][dy][dx], dx fastest.  Network: 75 -> 32 (ReLU) -> 32 (ReLU) -> 1,
+ * p = sigmoid(z); parameters as one float vector of 3521 entries: W1[32][75],
+ * b1[32], W2[32][32], b2[32], w3[32], b3.  Label: the plain scheme's
+ * largest |omega_m/gamma_m - 1| over every reconstructed field of both
+ * passes (Step 3), compared with a threshold delta. */
+
+/* feat_out: device float [cells][75] of the current state. */
+hweno_status hweno_indicator_features(hweno_solver* s, float* feat_out);
+/* dev_out: device float [cells], the label source above, of the current state. */
+hweno_status hweno_indicator_labels(hweno_solver* s, float* dev_out);
+/* Load trained parameters (host float[nparams], nparams = 3521) as FP16
+ * tensor-core weights and switch the solver to the learned path: from then
+ * on hweno_step / hweno_advance evaluate the network once per step on u^n,
+ * mark cells with p > p_threshold troubled, dilate the mark by one cell, and
+ * let every warp whose 32 cells are all unmarked reconstruct with p0. */
+hweno_status hweno_indicator_load(hweno_solver* s, const float* params, int nparams, double p_threshold);
+/* Back to the plain nonlinear path everywhere. */
+hweno_status hweno_indicator_off(hweno_solver* s);
+/* Run the network on the current state: smooth_out[cells] = 1 where the
+ * linear path is allowed (after dilation), troubled_out[cells] = 1 where the
+ * network itself marks the cell; device uint8 buffers, either may be NULL. */
+hweno_status hweno_indicator_mask(hweno_solver* s, void* smooth_out, void* troubled_out);
+
+/* Training on the GPU (FP32 master parameters, Adam with beta1 0.9,
+ * beta2 0.999, eps 1e-8).  The loss is the class-weighted binary cross
+ * entropy (positives weighted by pos_weight), mean over the minibatch.
+ * feat/dev are device float arrays [N][75] and [N]; idx is a device int32
+ * array [B] selecting the minibatch (the caller draws the permutation). */
+typedef struct hweno_mlp hweno_mlp;
+hweno_status hweno_mlp_create(int max_batch, void* cuda_stream, hweno_mlp** out);
+void hweno_mlp_destroy(hweno_mlp* m);
+/* Set the parameters (host float[3521]) and reset the Adam state. */
+hweno_status hweno_mlp_set_params(hweno_mlp* m, const float* params);
+hweno_status hweno_mlp_get_params(hweno_mlp* m, float* params);
+/* Loss and gradient (host float[3521]) of one minibatch, no update. */
+hweno_status hweno_mlp_gradient(hweno_mlp* m, const float* feat, const float* dev, const int* idx, int B,
+                                double delta, double pos_weight, float* grad_out, double* loss_out);
+/* One Adam step on one minibatch (asynchronous on the mlp's stream). */
+hweno_status hweno_mlp_train_step(hweno_mlp* m, const float* feat, const float* dev, const int* idx, int B,
+                                  double delta, double pos_weight, double lr);
+/* Mean of the minibatch losses since the last call (synchronises). */
+hweno_status hweno_mlp_mean_loss(hweno_mlp* m, double* loss);
+/* FP32 probabilities prob[n] (device) of n samples feat[n][75] (device). */
+hweno_status hweno_mlp_predict(hweno_mlp* m, const float* feat, long long n, float* prob);
 
 /* ---- Allocation-free step (the paper has no counterpart: this serves
  * callers that cannot allocate device memory when they need a step, e.g. a

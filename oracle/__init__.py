@@ -142,6 +142,8 @@ def lib():
         L.or_recon_cell_2d.argtypes = [pp, dp, C.c_double, C.c_double, dp]
         L.or_euler_jacobian.argtypes = [C.c_int, C.c_int, dp, C.c_double, dp]
         L.or_euler_eigen.argtypes = [C.c_int, C.c_int, dp, C.c_double, dp, dp]
+        L.or_weight_deviation.argtypes = [pp, dp, dp]
+        L.or_padded_state.argtypes = [pp, dp, dp]
         _lib = L
     return _lib
 
@@ -249,3 +251,23 @@ def euler_eigen(dim: int, direction: int, U, gamma_gas: float = 1.4):
     R, L = np.zeros(n * n), np.zeros(n * n)
     lib().or_euler_eigen(dim, direction, _ptr(u), gamma_gas, _ptr(R), _ptr(L))
     return R.reshape(n, n), L.reshape(n, n)
+
+
+def weight_deviation(prob: Problem, U) -> np.ndarray:
+    """Per cell max |omega_m/gamma_m - 1| of the plain scheme's weights (label source)."""
+    U = _state(prob, U)
+    dev = np.zeros(U.shape[1:])
+    ps = prob._c()
+    if lib().or_weight_deviation(C.byref(ps), _ptr(U), _ptr(dev)):
+        raise RuntimeError("or_weight_deviation failed")
+    return dev
+
+
+def padded_state(prob: Problem, U) -> np.ndarray:
+    U = _state(prob, U)
+    shape = (prob.nfields, prob.ny + 4, prob.nx + 4) if prob.dim == 2 else (prob.nfields, prob.nx + 4)
+    out = np.zeros(shape)
+    ps = prob._c()
+    if lib().or_padded_state(C.byref(ps), _ptr(U), _ptr(out)):
+        raise RuntimeError("or_padded_state failed")
+    return out

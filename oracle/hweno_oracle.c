@@ -869,3 +869,81 @@ int or_run(const or_problem* p, double* U, double t_final, int max_steps, double
   if (steps_out) *steps_out = steps;
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned troubled-cell indicator (not part of the paper): the training     */
+/* label and the padded state the features are read from.                   */
+/* ------------------------------------------------------------------------ */
+/* Per cell, the largest |omega_m / gamma_m - 1| of the plain scheme's
+ * nonlinear weights (Sec. 2.1 / 2.2 Step 3) over every reconstructed field:
+ * the components (component-wise) or the characteristic fields of both
+ * passes (Remark 1).  dev has one value per cell. */
+int or_weight_deviation(const or_problem* p, const double* U, double* dev) {
+  if (check_problem(p)) return -1;
+  build_maps();
+  padded_t P;
+  if (make_padded(p, U, &P)) return -1;
+  const int nc = P.nc, nlin = p->dim == 1 ? 2 : 4;
+  const double dx = (p->xhi - p->xlo) / p->nx;
+  const double dy = p->dim == 2 ? (p->yhi - p->ylo) / p->ny : 1.0;
+  const int chr = p->equation == OR_EQ_EULER && p->charwise;
+  for (int j = 0; j < P.ny; ++j)
+    for (int i = 0; i < P.nx; ++i) {
+      double worst = 0.0;
+      const int npass = chr ? p->dim : 1;
+      for (int pass = 0; pass < npass; ++pass) {
+        double R[16], L[16];
+        double w[4][17];
+        int nin = p->dim == 1 ? 5 : 17;
+        double q[4][17];
+        if (p->dim == 1) {
+          for (int k = 0; k < nc; ++k) {
+            q[k][0] = *pcell(&P, k, i - 1, 0);
+            q[k][1] = *pcell(&P, k, i, 0);
+            q[k][2] = *pcell(&P, k, i + 1, 0);
+            q[k][3] = *pcell(&P, nc + k, i - 1, 0);
+            q[k][4] = *pcell(&P, nc + k, i + 1, 0);
+          }
+        } else {
+          for (int k = 0; k < nc; ++k) gather_q(&P, k, i, j, q[k]);
+        }
+        if (chr) {
+          double U0[4];
+          for (int k = 0; k < nc; ++k) U0[k] = q[k][p->dim == 1 ? 1 : 4];
+          or_euler_eigen(p->dim, pass, U0, p->gamma_gas, R, L);
+          for (int s = 0; s < nin; ++s) {
+            double x[4], y[4];
+            for (int k = 0; k < nc; ++k) x[k] = q[k][s];
+            matvec(nc, L, x, y);
+            for (int k = 0; k < nc; ++k) w[k][s] = y[k];
+          }
+        } else {
+          for (int k = 0; k < nc; ++k)
+            for (int s = 0; s < nin; ++s) w[k][s] = q[k][s];
+        }
+        for (int k = 0; k < nc; ++k) {
+          double out[48], *om;
+          if (p->dim == 1) { or_recon_cell_1d(p, w[k], dx, out); om = out + 5; }
+          else { or_recon_cell_2d(p, w[k], dx, dy, out); om = out + 38; }
+          for (int m = 0; m <= nlin; ++m) {
+            const double d = fabs(om[m] / p->lin_w[m] - 1.0);
+            if (d > worst || d != d) worst = d;
+          }
+        }
+      }
+      dev[(size_t)j * P.nx + i] = worst;
+    }
+  free(P.a);
+  return 0;
+}
+
+/* The state with its 2 ghost layers filled (the boundary rules above):
+ * out[f][ny+4][nx+4] in 2D, out[f][nx+4] in 1D. */
+int or_padded_state(const or_problem* p, const double* U, double* out) {
+  if (check_problem(p)) return -1;
+  padded_t P;
+  if (make_padded(p, U, &P)) return -1;
+  memcpy(out, P.a, sizeof(double) * (size_t)P.nf * P.px * P.py);
+  free(P.a);
+  return 0;
+}

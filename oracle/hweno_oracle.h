@@ -95,6 +95,14 @@ int or_step(const or_problem* p, double* U, double dt, double ax, double ay);
 int or_run(const or_problem* p, double* U, double t_final, int max_steps,
            double* t_out, int* steps_out);
 
+/* Learned troubled-cell indicator (not in the paper).  dev[cell] = the
+ * largest |omega_m / gamma_m - 1| of the plain scheme's nonlinear weights
+ * over every reconstructed field (both passes for 2D characteristic Euler):
+ * the label source.  or_padded_state returns the state with its ghost
+ * layers: out[f][ny+4][nx+4] (2D) or out[f][nx+4] (1D). */
+int or_weight_deviation(const or_problem* p, const double* U, double* dev);
+int or_padded_state(const or_problem* p, const double* U, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,6 +4,7 @@
 // against the caller's stream, the device-resident time-step control and the
 // CUDA graph that replays whole SSP-RK3 steps (ctl_begin, stage 1, stage 2,
 // stage 3, ctl_end).  All arithmetic of the scheme runs in the kernels.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -71,7 +72,8 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
   if (c->weight_pow != 1 && c->weight_pow != 2) return fail(HWENO_ERR_ARG, "weight_pow must be 1 or 2");
   if (!(c->cfl > 0.0)) return fail(HWENO_ERR_ARG, "cfl must be positive");
   if (c->dt_rule != HWENO_DT_CFL && c->dt_rule != HWENO_DT_CFL_DX53) return fail(HWENO_ERR_ARG, "bad dt_rule");
-  if (c->precision != HWENO_FP64 && c->precision != HWENO_FP32) return fail(HWENO_ERR_ARG, "bad precision");
+  if (c->precision != HWENO_FP64 && c->precision != HWENO_FP32 && c->precision != HWENO_FP32_IND64)
+    return fail(HWENO_ERR_ARG, "bad precision");
   const int nsides = c->dim == 1 ? 2 : 4;
   for (int k = 0; k < nsides; ++k)
     if (c->bc[k] < 0 || c->bc[k] > 3) return fail(HWENO_ERR_ARG, "bad boundary condition on side %d", k);
@@ -121,12 +123,20 @@ struct Engine {
   int pev_used = 0;
   double prof_stage_ms = 0.0, prof_total_ms = 0.0;
   long long prof_stage_launches = 0, prof_launches = 0;
+  // learned troubled-cell indicator (2D): FP16 weights and the per-step masks
+  bool learned = false;
+  __half* mlp_w = nullptr;            // W1h [32][80] then W2h [32][32]
+  float* mlp_bias = nullptr;          // b1, b2, w3, b3
+  unsigned char* troubled = nullptr;  // network output per cell
+  unsigned char* smooth = nullptr;    // dilated complement: 1 = linear path
+  float z_thresh = 0.f;
 
   ~Engine() {
     for (cudaEvent_t e : pev) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
     cudaFree(S); cudaFree(A); cudaFree(B); cudaFree(H);
     cudaFree(ctl); cudaFree(ctl_manual); cudaFree(inst_d); cudaFree(tasks_d); cudaFree(alpha_op);
+    cudaFree(mlp_w); cudaFree(mlp_bias); cudaFree(troubled); cudaFree(smooth);
     if (ctl_host) cudaFreeHost(ctl_host);
     if (ev) cudaEventDestroy(ev);
     if (own) cudaStreamDestroy(own);
@@ -245,6 +255,7 @@ struct Engine {
       a.grid = grid; a.ctl = c; a.ax_op = ax; a.ay_op = ay; a.stage = s;
       a.gamma_gas = cfg.gamma_gas; a.adv_x = cfg.adv_x; a.adv_y = cfg.adv_y; a.wp = wp;
       a.plane = cells;
+      a.smooth = learned && s > 0 ? smooth : nullptr;
       HW_CK(hw::launch_stage2d(prec, cfg.equation, cfg.charwise, a, num_sms, own));
     }
     return HWENO_OK;
@@ -269,8 +280,15 @@ struct Engine {
     return HWENO_OK;
   }
 
+  hweno_status run_indicator() {
+    hw::MlpDev m{mlp_w, mlp_w + 32 * 80, mlp_bias, z_thresh};
+    HW_CK(hw::launch_mlp_infer2d(prec, cfg.equation, S, grid, cells, m, troubled, smooth, num_sms, own));
+    return HWENO_OK;
+  }
+
   hweno_status one_step() {
     HW_CK(hw::launch_ctl_begin(ctl, n_inst, dim, own));
+    if (learned) HW_TRY(run_indicator());  // once per step, on u^n; reused by the 3 stages
     HW_TRY(rk_stages(ctl));
     HW_CK(hw::launch_ctl_end(ctl, n_inst, own));
     return HWENO_OK;
@@ -408,6 +426,7 @@ struct Engine {
       return fail(HWENO_ERR_ARG, "dt and alpha must be finite and non-negative");
     HW_TRY(enter());
     HW_CK(cudaStreamSynchronize(own));
+    if (learned) HW_TRY(run_indicator());
     for (int k = 0; k < n_inst; ++k) {
       ctl_host[k] = ctl_init[k];
       ctl_host[k].dt = dt;
@@ -434,9 +453,80 @@ struct Engine {
     HW_TRY(stage(0, S, L, ctl, ax[0], ay, dh));
     return leave();
   }
+
+  hweno_status load_indicator(const float* theta, int n, double p_threshold) {
+    if (dim != 2) return fail(HWENO_ERR_ARG, "the learned indicator serves 2D solvers");
+    if (!theta || n != hw::kMlpParams) return fail(HWENO_ERR_ARG, "expected %d network parameters", hw::kMlpParams);
+    if (!(p_threshold > 0.0 && p_threshold < 1.0)) return fail(HWENO_ERR_ARG, "threshold must lie in (0, 1)");
+    for (int k = 0; k < n; ++k)
+      if (!std::isfinite(theta[k])) return fail(HWENO_ERR_ARG, "parameter %d is not finite", k);
+    if (!mlp_w) {
+      HW_CK(hw::prepare_mlp_infer2d());
+      HW_CK(cudaMalloc(&mlp_w, sizeof(__half) * (32 * 80 + 32 * 32)));
+      HW_CK(cudaMalloc(&mlp_bias, sizeof(float) * 97));
+      HW_CK(cudaMalloc(&troubled, (size_t)cells));
+      HW_CK(cudaMalloc(&smooth, (size_t)cells));
+    }
+    std::vector<__half> w(32 * 80 + 32 * 32);
+    std::vector<float> b(97);
+    for (int r = 0; r < 32; ++r)
+      for (int c = 0; c < 80; ++c) w[r * 80 + c] = __float2half(c < 75 ? theta[r * 75 + c] : 0.0f);
+    const int ob1 = 32 * 75, ow2 = ob1 + 32, ob2 = ow2 + 32 * 32, ow3 = ob2 + 32, ob3 = ow3 + 32;
+    for (int k = 0; k < 32 * 32; ++k) w[32 * 80 + k] = __float2half(theta[ow2 + k]);
+    for (int k = 0; k < 32; ++k) {
+      b[k] = theta[ob1 + k];
+      b[32 + k] = theta[ob2 + k];
+      b[64 + k] = theta[ow3 + k];
+    }
+    b[96] = theta[ob3];
+    HW_CK(cudaStreamSynchronize(own));
+    HW_CK(cudaMemcpy(mlp_w, w.data(), sizeof(__half) * w.size(), cudaMemcpyHostToDevice));
+    HW_CK(cudaMemcpy(mlp_bias, b.data(), sizeof(float) * b.size(), cudaMemcpyHostToDevice));
+    z_thresh = (float)std::log(p_threshold / (1.0 - p_threshold));
+    learned = true;
+    drop_graph();
+    return HWENO_OK;
+  }
+
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
 };
 
 struct hweno_solver { Engine e; };
+
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1/2, 1/2] (weights sum to 1): roots
+// of P_n by Newton's method from the Chebyshev-like initial guesses, weights
+// 1 / ((1 - x^2) P_n'(x)^2) on [-1, 1], halved.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      const double pn = n == 1 ? z : p1, pm = n == 1 ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      const double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * z;
+    w[i] = 0.5 * 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+}  // namespace
 struct hweno_batch { Engine e; };
 
 extern "C" {
@@ -590,3 +680,224 @@ hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, voi
 }
 
 }  // extern "C"
+
+// ---- learned troubled-cell indicator ----
+struct hweno_mlp {
+  cudaStream_t stream = nullptr;
+  int max_batch = 0;
+  float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  hw::MlpWork w{};
+  int t = 0;
+  ~hweno_mlp() {
+    cudaFree(theta); cudaFree(m); cudaFree(v); cudaFree(grad);
+    cudaFree(w.h1); cudaFree(w.dh1); cudaFree(w.h2); cudaFree(w.dh2); cudaFree(w.dz); cudaFree(w.loss);
+    cudaFree(w.loss_acc);
+  }
+};
+
+extern "C" {
+
+hweno_status hweno_indicator_load(hweno_solver* s, const float* theta, int nparams, double p_threshold) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  return s->e.load_indicator(theta, nparams, p_threshold);
+}
+
+hweno_status hweno_indicator_off(hweno_solver* s) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  s->e.learned = false;
+  s->e.drop_graph();
+  return HWENO_OK;
+}
+
+hweno_status hweno_indicator_mask(hweno_solver* s, void* smooth_out, void* troubled_out) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  Engine& e = s->e;
+  if (!e.learned) return fail(HWENO_ERR_STATE, "no indicator loaded");
+  if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(e.enter());
+  HW_TRY(e.run_indicator());
+  if (smooth_out) HW_CK(cudaMemcpyAsync(smooth_out, e.smooth, (size_t)e.cells, cudaMemcpyDeviceToDevice, e.own));
+  if (troubled_out)
+    HW_CK(cudaMemcpyAsync(troubled_out, e.troubled, (size_t)e.cells, cudaMemcpyDeviceToDevice, e.own));
+  return e.leave();
+}
+
+hweno_status hweno_indicator_features(hweno_solver* s, float* feat_out) {
+  if (!s || !feat_out) return fail(HWENO_ERR_ARG, "solver or output is NULL");
+  Engine& e = s->e;
+  if (e.dim != 2) return fail(HWENO_ERR_ARG, "the learned indicator serves 2D solvers");
+  if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(e.enter());
+  HW_CK(hw::launch_features2d(e.prec, e.cfg.equation, e.S, e.grid, e.cells, feat_out, e.num_sms, e.own));
+  return e.leave();
+}
+
+hweno_status hweno_indicator_labels(hweno_solver* s, float* dev_out) {
+  if (!s || !dev_out) return fail(HWENO_ERR_ARG, "solver or output is NULL");
+  Engine& e = s->e;
+  if (e.dim != 2) return fail(HWENO_ERR_ARG, "the learned indicator serves 2D solvers");
+  if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(e.enter());
+  HW_CK(hw::launch_labels2d(e.prec, e.cfg.equation, e.cfg.charwise, e.S, e.grid, e.cells, e.wp, e.cfg.gamma_gas,
+                            dev_out, e.num_sms, e.own));
+  return e.leave();
+}
+
+hweno_status hweno_mlp_create(int max_batch, void* cuda_stream, hweno_mlp** out) {
+  if (!out) return fail(HWENO_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > (1 << 24)) return fail(HWENO_ERR_ARG, "max_batch must be in [1, 2^24]");
+  hweno_mlp* m = new (std::nothrow) hweno_mlp();
+  if (!m) return fail(HWENO_ERR_OOM, "host allocation failed");
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  m->max_batch = max_batch;
+  const size_t P = sizeof(float) * hw::kMlpParams, H = sizeof(float) * 32 * (size_t)max_batch;
+  cudaError_t e = cudaSuccess;
+  float** bufs[] = {&m->theta, &m->m, &m->v, &m->grad};
+  for (float** b : bufs) if (e == cudaSuccess) e = cudaMalloc(b, P);
+  float** hb[] = {&m->w.h1, &m->w.dh1, &m->w.h2, &m->w.dh2};
+  for (float** b : hb) if (e == cudaSuccess) e = cudaMalloc(b, H);
+  if (e == cudaSuccess) e = cudaMalloc(&m->w.dz, sizeof(float) * max_batch);
+  if (e == cudaSuccess) e = cudaMalloc(&m->w.loss, sizeof(float) * max_batch);
+  if (e == cudaSuccess) e = cudaMalloc(&m->w.loss_acc, sizeof(float) * 2);
+  if (e == cudaSuccess) e = cudaMemset(m->w.loss_acc, 0, sizeof(float) * 2);
+  if (e != cudaSuccess) {
+    delete m;
+    return fail(e == cudaErrorMemoryAllocation ? HWENO_ERR_OOM : HWENO_ERR_CUDA, "%s", cudaGetErrorString(e));
+  }
+  *out = m;
+  return HWENO_OK;
+}
+
+void hweno_mlp_destroy(hweno_mlp* m) { delete m; }
+
+hweno_status hweno_mlp_set_params(hweno_mlp* m, const float* theta) {
+  if (!m || !theta) return fail(HWENO_ERR_ARG, "mlp or parameters NULL");
+  HW_CK(cudaStreamSynchronize(m->stream));
+  HW_CK(cudaMemcpy(m->theta, theta, sizeof(float) * hw::kMlpParams, cudaMemcpyHostToDevice));
+  HW_CK(cudaMemset(m->m, 0, sizeof(float) * hw::kMlpParams));
+  HW_CK(cudaMemset(m->v, 0, sizeof(float) * hw::kMlpParams));
+  HW_CK(cudaMemset(m->w.loss_acc, 0, sizeof(float) * 2));
+  m->t = 0;
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_get_params(hweno_mlp* m, float* theta) {
+  if (!m || !theta) return fail(HWENO_ERR_ARG, "mlp or output NULL");
+  HW_CK(cudaStreamSynchronize(m->stream));
+  HW_CK(cudaMemcpy(theta, m->theta, sizeof(float) * hw::kMlpParams, cudaMemcpyDeviceToHost));
+  return HWENO_OK;
+}
+
+static hweno_status mlp_check(hweno_mlp* m, const float* feat, const float* dev, const int* idx, int B) {
+  if (!m || !feat || !dev || !idx) return fail(HWENO_ERR_ARG, "NULL argument");
+  if (B < 1 || B > m->max_batch) return fail(HWENO_ERR_ARG, "batch size %d outside [1, %d]", B, m->max_batch);
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_gradient(hweno_mlp* m, const float* feat, const float* dev, const int* idx, int B,
+                                double delta, double pos_weight, float* grad_out, double* loss_out) {
+  HW_TRY(mlp_check(m, feat, dev, idx, B));
+  if (!grad_out) return fail(HWENO_ERR_ARG, "grad_out is NULL");
+  HW_CK(cudaMemsetAsync(m->w.loss_acc, 0, sizeof(float) * 2, m->stream));
+  HW_CK(hw::launch_mlp_train(m->theta, feat, dev, idx, B, (float)delta, (float)pos_weight, m->w, m->grad, m->stream));
+  float acc[2];
+  HW_CK(cudaMemcpyAsync(grad_out, m->grad, sizeof(float) * hw::kMlpParams, cudaMemcpyDeviceToHost, m->stream));
+  HW_CK(cudaMemcpyAsync(acc, m->w.loss_acc, sizeof acc, cudaMemcpyDeviceToHost, m->stream));
+  HW_CK(cudaStreamSynchronize(m->stream));
+  if (loss_out) *loss_out = acc[0];
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_train_step(hweno_mlp* m, const float* feat, const float* dev, const int* idx, int B,
+                                  double delta, double pos_weight, double lr) {
+  HW_TRY(mlp_check(m, feat, dev, idx, B));
+  if (!(lr > 0.0)) return fail(HWENO_ERR_ARG, "learning rate must be positive");
+  HW_CK(hw::launch_mlp_train(m->theta, feat, dev, idx, B, (float)delta, (float)pos_weight, m->w, m->grad, m->stream));
+  m->t += 1;
+  HW_CK(hw::launch_mlp_adam(m->theta, m->m, m->v, m->grad, (float)lr, m->t, m->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_mean_loss(hweno_mlp* m, double* loss) {
+  if (!m || !loss) return fail(HWENO_ERR_ARG, "NULL argument");
+  float acc[2];
+  HW_CK(cudaMemcpyAsync(acc, m->w.loss_acc, sizeof acc, cudaMemcpyDeviceToHost, m->stream));
+  HW_CK(cudaMemsetAsync(m->w.loss_acc, 0, sizeof(float) * 2, m->stream));
+  HW_CK(cudaStreamSynchronize(m->stream));
+  *loss = acc[1] > 0.f ? acc[0] / acc[1] : 0.0;
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_predict(hweno_mlp* m, const float* feat, long long n, float* prob) {
+  if (!m || !feat || !prob || n < 1) return fail(HWENO_ERR_ARG, "bad argument");
+  int dev = 0, sms = 148;
+  HW_CK(cudaGetDevice(&dev));
+  HW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  HW_CK(hw::launch_mlp_predict(m->theta, feat, n, prob, sms, m->stream));
+  return HWENO_OK;
+}
+
+}  // extern "C"
+
+extern "C" hweno_status hweno_project(hweno_solver* s, hweno_u0_fn u0, void* ctx, int nq) {
+  if (!s || !u0) return fail(HWENO_ERR_ARG, "solver or u0 is NULL");
+  if (nq < 1 || nq > 16) return fail(HWENO_ERR_ARG, "nq must lie in [1, 16]");
+  Engine& e = s->e;
+  if (e.n_inst != 1) return fail(HWENO_ERR_ARG, "projection serves single-grid solvers");
+  const hweno_config& c = e.cfg;
+  std::vector<double> gx, gw;
+  gauss_legendre(nq, gx, gw);
+  const int nc = e.nc, nx = c.nx, ny = c.dim == 2 ? c.ny : 1;
+  const double dx = (c.xhi - c.xlo) / nx, dy = c.dim == 2 ? (c.yhi - c.ylo) / ny : 1.0;
+  const size_t cells = (size_t)nx * ny;
+  std::vector<double> U((size_t)e.nf * cells, 0.0);
+  // one callback per row: every quadrature / face point of the row at once
+  const int per_cell = c.dim == 2 ? nq * nq + 4 * nq : nq + 2;
+  std::vector<double> X((size_t)nx * per_cell), Y((size_t)nx * per_cell), V((size_t)nx * per_cell * nc);
+  for (int j = 0; j < ny; ++j) {
+    const double yc = c.dim == 2 ? c.ylo + (j + 0.5) * dy : 0.0;
+    size_t p = 0;
+    for (int i = 0; i < nx; ++i) {
+      const double xc = c.xlo + (i + 0.5) * dx;
+      if (c.dim == 1) {
+        for (int a = 0; a < nq; ++a) { X[p] = xc + dx * gx[a]; Y[p++] = 0.0; }
+        X[p] = xc - 0.5 * dx; Y[p++] = 0.0;
+        X[p] = xc + 0.5 * dx; Y[p++] = 0.0;
+      } else {
+        for (int b = 0; b < nq; ++b)
+          for (int a = 0; a < nq; ++a) { X[p] = xc + dx * gx[a]; Y[p++] = yc + dy * gx[b]; }
+        for (int b = 0; b < nq; ++b) { X[p] = xc - 0.5 * dx; Y[p++] = yc + dy * gx[b]; }
+        for (int b = 0; b < nq; ++b) { X[p] = xc + 0.5 * dx; Y[p++] = yc + dy * gx[b]; }
+        for (int a = 0; a < nq; ++a) { X[p] = xc + dx * gx[a]; Y[p++] = yc - 0.5 * dy; }
+        for (int a = 0; a < nq; ++a) { X[p] = xc + dx * gx[a]; Y[p++] = yc + 0.5 * dy; }
+      }
+    }
+    u0((int)p, X.data(), Y.data(), V.data(), ctx);
+    for (size_t q = 0; q < p * nc; ++q)
+      if (!std::isfinite(V[q])) return fail(HWENO_ERR_ARG, "u0 returned a non-finite value");
+    for (int i = 0; i < nx; ++i) {
+      const double* v = V.data() + (size_t)i * per_cell * nc;
+      const size_t cell = (size_t)j * nx + i;
+      for (int k = 0; k < nc; ++k) {
+        double avg = 0.0, vb = 0.0, wb = 0.0;
+        if (c.dim == 1) {
+          for (int a = 0; a < nq; ++a) avg += gw[a] * v[a * nc + k];
+          vb = (v[(nq + 1) * nc + k] - v[nq * nc + k]) / dx;  // mean of u_x over the cell
+        } else {
+          for (int b = 0; b < nq; ++b)
+            for (int a = 0; a < nq; ++a) avg += gw[a] * gw[b] * v[(b * nq + a) * nc + k];
+          const int o = nq * nq;
+          for (int b = 0; b < nq; ++b) vb += gw[b] * (v[(o + nq + b) * nc + k] - v[(o + b) * nc + k]);
+          for (int a = 0; a < nq; ++a) wb += gw[a] * (v[(o + 3 * nq + a) * nc + k] - v[(o + 2 * nq + a) * nc + k]);
+        }
+        U[(size_t)k * cells + cell] = avg;
+        U[(size_t)(nc + k) * cells + cell] = vb;
+        if (c.dim == 2) U[(size_t)(2 * nc + k) * cells + cell] = wb;
+      }
+    }
+  }
+  if (e.prec == HWENO_FP64) return e.set_state(U.data(), 0);
+  std::vector<float> Uf(U.begin(), U.end());
+  return e.set_state(Uf.data(), 0);
+}

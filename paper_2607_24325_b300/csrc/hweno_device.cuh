@@ -40,11 +40,48 @@ __host__ __device__ inline WeightsT<T> make_weights(const WeightParams& w) {
 template <typename T>
 __device__ __forceinline__ T fabs_t(T x) { return x < T(0) ? -x : x; }
 
-// omega-tilde_m = gamma_m (1 + tau^2 / (beta_m^{1|2} + eps))  (Eq. nonlinear-weights)
-template <typename T>
-__device__ __forceinline__ T wtilde(T gam, T tau2, T beta, const WeightsT<T>& w) {
-  const T b = w.pow2 ? beta * beta : beta;
-  return gam * (T(1) + tau2 / (b + w.eps));
+// Reciprocal and quotient: IEEE in FP64; in FP32 the fast approximate forms
+// (a few ulp), far below the FP32 stencil's own conditioning.
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+
+// Nonlinear weights of Eq. (nonlinear-weights) / (nonlinear-weights-2D) for
+// one target polynomial and NL linear ones: given beta_0..beta_NL and tau,
+// returns r = omega_0 / gamma_0 and omega_1..omega_NL (om[0] unused).
+// w~_m = gamma_m (1 + tau^2/d_m), d_m = beta_m^{1|2} + eps, omega = w~ / sum w~.
+// FP64 uses the equal form w~_m prod_k d_k = gamma_m (d_m + tau^2) prod_{k!=m} d_k,
+// which needs one division instead of NL+2 (FP64 division is costly on B300);
+// FP32 keeps the quotients (products of d could overflow its range).
+template <typename T, int NL>
+__device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<T>& w, T& r, T* om) {
+  const T t2 = tau * tau;
+  T d[NL + 1];
+#pragma unroll
+  for (int m = 0; m <= NL; ++m) d[m] = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
+  T e[NL + 1];
+  if constexpr (sizeof(T) == 8) {
+    T pre[NL + 1], suf[NL + 1];
+    pre[0] = T(1);
+#pragma unroll
+    for (int m = 1; m <= NL; ++m) pre[m] = pre[m - 1] * d[m - 1];
+    suf[NL] = T(1);
+#pragma unroll
+    for (int m = NL - 1; m >= 0; --m) suf[m] = suf[m + 1] * d[m + 1];
+#pragma unroll
+    for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (d[m] + t2) * (pre[m] * suf[m]);
+  } else {
+#pragma unroll
+    for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (T(1) + div_t(t2, d[m]));
+  }
+  T s = e[0];
+#pragma unroll
+  for (int m = 1; m <= NL; ++m) s += e[m];
+  const T inv = rcp_t(s);
+  r = e[0] * inv * w.inv_g0;
+#pragma unroll
+  for (int m = 1; m <= NL; ++m) om[m] = e[m] * inv;
 }
 
 // ---------------------------------------------------------------------------
@@ -56,9 +93,9 @@ __device__ __forceinline__ T wtilde(T gam, T tau2, T beta, const WeightsT<T>& w)
 template <typename T>
 struct Rec1 { T uL, uR, dL, dR, vh; };
 
-template <typename T>
+template <typename T, bool W64 = false>
 __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T idx,
-                                          const WeightsT<T>& w) {
+                                          const WeightsT<T>& w, const WeightsT<double>* w64 = nullptr) {
   const T a = dx * vm, b = dx * vp;
   const T s = um + up, dd = up - um, ab = a + b, ba = b - a;
   // Appendix A: p0 = sum_l c_l xi^l, xi = (x - x_i)/dx
@@ -72,16 +109,31 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
   T r, w1, w2;  // r = omega_0 / gamma_0
   if (w.linear) {
     r = T(1); w1 = w.g[1]; w2 = w.g[2];
+  } else if constexpr (W64) {
+    // mixed precision: the indicator coefficients, indicators and weights in FP64
+    const double A = (double)dx * (double)vm, Bv = (double)dx * (double)vp;
+    const double S = (double)um + (double)up, D = (double)up - (double)um, AB = A + Bv, BA = Bv - A;
+    const double e1 = 13.0 / 16.0 * D - 5.0 / 16.0 * AB;
+    const double e2 = 5.0 / 4.0 * S - 5.0 / 2.0 * (double)u0 - 3.0 / 8.0 * BA;
+    const double e3 = 0.25 * (AB - D);
+    const double e4 = (double)u0 - 0.5 * S + 0.25 * BA;
+    const double f1 = (double)u0 - (double)um, f2 = (double)up - (double)u0;
+    double beta[3] = {e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4, f1 * f1, f2 * f2};
+    const double tau = 0.5 * (fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
+    double r64, om[3];
+    nl_weights<double, 2>(beta, tau, *w64, r64, om);
+    r = (T)r64; w1 = (T)om[1]; w2 = (T)om[2];
   } else {
     // Step 2: beta = sum_l (l! c_l)^2
-    const T b0 = c1 * c1 + T(4) * c2 * c2 + T(36) * c3 * c3 + T(576) * c4 * c4;
-    const T b1 = d1 * d1, b2 = d2 * d2;
+    T beta[3];
+    beta[0] = c1 * c1 + T(4) * c2 * c2 + T(36) * c3 * c3 + T(576) * c4 * c4;
+    beta[1] = d1 * d1;
+    beta[2] = d2 * d2;
     // Step 3
-    const T tau = T(0.5) * (fabs_t(b0 - b1) + fabs_t(b0 - b2));
-    const T t2 = tau * tau;
-    const T e0 = wtilde(w.g[0], t2, b0, w), e1 = wtilde(w.g[1], t2, b1, w), e2 = wtilde(w.g[2], t2, b2, w);
-    const T inv = T(1) / (e0 + e1 + e2);
-    r = e0 * inv * w.inv_g0; w1 = e1 * inv; w2 = e2 * inv;
+    const T tau = T(0.5) * (fabs_t(beta[0] - beta[1]) + fabs_t(beta[0] - beta[2]));
+    T om[3];
+    nl_weights<T, 2>(beta, tau, w, r, om);
+    w1 = om[1]; w2 = om[2];
   }
   // Eq. (hweno-reconstruction-1D): u_i = r (p0 - g1 p1 - g2 p2) + w1 p1 + w2 p2
   const T k0 = r * (c0 - (w.g[1] + w.g[2]) * u0) + (w1 + w2) * u0;
@@ -111,32 +163,32 @@ struct Eig {
 template <typename T>
 __device__ __forceinline__ Eig<T> eig1(T r, T m, T E, T g) {
   Eig<T> e;
-  const T ir = T(1) / r;
+  const T ir = rcp_t(r);
   e.u = m * ir;
   e.v = T(0);
   e.q2h = T(0.5) * e.u * e.u;
   const T p = (g - T(1)) * (E - m * e.u * T(0.5));
   const T c2 = g * p * ir;
   e.c = sqrt(c2);
-  e.ic = T(1) / e.c;
+  e.ic = rcp_t(e.c);
   e.H = (E + p) * ir;
-  e.b1 = (g - T(1)) / c2;
+  e.b1 = (g - T(1)) * e.ic * e.ic;
   return e;
 }
 
 template <typename T>
 __device__ __forceinline__ Eig<T> eig2(T r, T mx, T my, T E, T g) {
   Eig<T> e;
-  const T ir = T(1) / r;
+  const T ir = rcp_t(r);
   e.u = mx * ir;
   e.v = my * ir;
   e.q2h = T(0.5) * (e.u * e.u + e.v * e.v);
   const T p = (g - T(1)) * (E - r * e.q2h);
   const T c2 = g * p * ir;
   e.c = sqrt(c2);
-  e.ic = T(1) / e.c;
+  e.ic = rcp_t(e.c);
   e.H = (E + p) * ir;
-  e.b1 = (g - T(1)) / c2;
+  e.b1 = (g - T(1)) * e.ic * e.ic;
   return e;
 }
 
@@ -191,7 +243,7 @@ __device__ __forceinline__ void r2_apply(const Eig<T>& e, const T* w, T* y) {
 // Flux f(U) and its directional derivative f'(U) V, 1D Euler.
 template <typename T>
 __device__ __forceinline__ void euler1_flux(const T* U, const T* V, T g, T* F, T* H) {
-  const T ir = T(1) / U[0];
+  const T ir = rcp_t(U[0]);
   const T u = U[1] * ir;
   const T p = (g - T(1)) * (U[2] - T(0.5) * U[1] * u);
   F[0] = U[1];
@@ -208,7 +260,7 @@ __device__ __forceinline__ void euler1_flux(const T* U, const T* V, T g, T* F, T
 template <int D, typename T>
 __device__ __forceinline__ void euler2_flux(const T* U, const T* V, const T* Wv, T g, T* F, T* HV,
                                             T* HW) {
-  const T ir = T(1) / U[0];
+  const T ir = rcp_t(U[0]);
   const T u = U[1] * ir, v = U[2] * ir;
   const T gm = g - T(1);
   const T p = gm * (U[3] - T(0.5) * (U[1] * u + U[2] * v));

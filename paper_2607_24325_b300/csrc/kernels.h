@@ -1,6 +1,7 @@
 // kernels.h -- host-side launch interface of the libhweno kernels.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "hweno_types.h"
@@ -40,7 +41,21 @@ struct Stage2Args {
   double gamma_gas, adv_x, adv_y;
   WeightParams wp;
   long long plane;        // nx * ny
+  const unsigned char* smooth;  // learned indicator: 1 = linear path allowed (nullptr: off)
 };
+
+// Learned troubled-cell indicator: per-sample training buffers and the
+// FP16 inference weights.
+struct MlpWork {
+  float *h1, *dh1, *h2, *dh2, *dz, *loss, *loss_acc;
+};
+struct MlpDev {
+  const __half* W1h;   // [32][80], columns 75..79 zero
+  const __half* W2h;   // [32][32]
+  const float* bias;   // b1[32], b2[32], w3[32], b3
+  float z_thresh;      // logit of the troubled-probability threshold
+};
+constexpr int kMlpParams = 3521;
 
 constexpr int kTile1 = 30;   // interior cells per warp task (32 lanes - 2 ring cells)
 
@@ -55,6 +70,20 @@ cudaError_t prepare_stage2d(int precision, int equation, int charwise);
 cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane,
                            double gamma_gas, double adv_x, double adv_y, Ctl* ctl, int num_sms,
                            cudaStream_t st);
+cudaError_t launch_features2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
+                              float* feat, int num_sms, cudaStream_t st);
+cudaError_t launch_labels2d(int precision, int equation, int charwise, const void* U, const Grid2& G,
+                            long long plane, const WeightParams& wp, double gamma_gas, float* dev, int num_sms,
+                            cudaStream_t st);
+cudaError_t launch_mlp_train(const float* theta, const float* feat, const float* dev, const int* idx, int B,
+                             float delta, float pos_weight, MlpWork& w, float* grad, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* g, float lr, int t, cudaStream_t st);
+cudaError_t launch_mlp_predict(const float* theta, const float* feat, long long N, float* prob, int num_sms,
+                               cudaStream_t st);
+cudaError_t prepare_mlp_infer2d();
+cudaError_t launch_mlp_infer2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
+                               const MlpDev& m, unsigned char* troubled, unsigned char* smooth, int num_sms,
+                               cudaStream_t st);
 cudaError_t launch_ctl_begin(Ctl* ctl, int n, int dim, cudaStream_t st);
 cudaError_t launch_ctl_end(Ctl* ctl, int n, cudaStream_t st);
 cudaError_t launch_ctl_commit_alpha(Ctl* ctl, int n, cudaStream_t st);

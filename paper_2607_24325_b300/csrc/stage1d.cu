@@ -68,7 +68,7 @@ __device__ __forceinline__ void lf_flux1(const T* um, const T* up, const T* vm, 
   }
 }
 
-template <typename T, int EQ, bool CHR>
+template <typename T, int EQ, bool CHR, bool W64>
 __global__ void __launch_bounds__(128) k_stage1d(const Stage1Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 3 : 1;
   const T* __restrict__ in = static_cast<const T*>(a.in);
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(128) k_stage1d(const Stage1Args a) {
   T* out = static_cast<T*>(a.out);
   T* __restrict__ hat = static_cast<T*>(a.hat);
   const WeightsT<T> w = make_weights<T>(a.wp);
+  const WeightsT<double> w64 = make_weights<double>(a.wp);
   const T g = (T)a.gamma_gas, adv = (T)a.adv;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(128) k_stage1d(const Stage1Args a) {
       T oL[3], oR[3], odL[3], odR[3], ov[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const Rec1<T> r = recon1<T>(Wm[k], W0[k], Wp[k], Zm[k], Zp[k], dx, idx, w);
+        const Rec1<T> r = recon1<T, W64>(Wm[k], W0[k], Wp[k], Zm[k], Zp[k], dx, idx, w, &w64);
         oL[k] = r.uL; oR[k] = r.uR; odL[k] = r.dL; odR[k] = r.dR; ov[k] = r.vh;
       }
       r1_apply(e, oL, uL); r1_apply(e, oR, uR); r1_apply(e, odL, dL); r1_apply(e, odR, dR);
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(128) k_stage1d(const Stage1Args a) {
     } else {
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        const Rec1<T> r = recon1<T>(um[k], ub[k], up[k], vm[k], vp[k], dx, idx, w);
+        const Rec1<T> r = recon1<T, W64>(um[k], ub[k], up[k], vm[k], vp[k], dx, idx, w, &w64);
         uL[k] = r.uL; uR[k] = r.uR; dL[k] = r.dL; dR[k] = r.dR; vh[k] = r.vh;
       }
     }
@@ -210,14 +211,14 @@ __global__ void __launch_bounds__(128) k_alpha1d(const T* __restrict__ U, long l
   }
 }
 
-template <typename T, int EQ, bool CHR>
+template <typename T, int EQ, bool CHR, bool W64 = false>
 static cudaError_t go1(const Stage1Args& a, int num_sms, cudaStream_t st) {
   const int warps = 4;
   long long blocks = (a.ntasks + warps - 1) / warps;
   const long long cap = (long long)num_sms * 16;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k_stage1d<T, EQ, CHR><<<(unsigned)blocks, 32 * warps, 0, st>>>(a);
+  k_stage1d<T, EQ, CHR, W64><<<(unsigned)blocks, 32 * warps, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -230,6 +231,12 @@ cudaError_t launch_stage1d(int precision, int equation, int charwise, const Stag
                                                : go1<double, HWENO_EQ_EULER, false>(a, num_sms, st);
     if (equation == HWENO_EQ_BURGERS) return go1<double, HWENO_EQ_BURGERS, false>(a, num_sms, st);
     return go1<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+  }
+  if (precision == HWENO_FP32_IND64) {
+    if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true, true>(a, num_sms, st)
+                                               : go1<float, HWENO_EQ_EULER, false, true>(a, num_sms, st);
+    if (equation == HWENO_EQ_BURGERS) return go1<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st);
+    return go1<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st);
   }
   if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true>(a, num_sms, st)
                                              : go1<float, HWENO_EQ_EULER, false>(a, num_sms, st);

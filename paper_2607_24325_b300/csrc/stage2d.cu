@@ -19,141 +19,10 @@
 #include <cuda_runtime.h>
 
 #include "hweno_device.cuh"
+#include "hweno_stencil2d.cuh"
 #include "kernels.h"
 
 namespace hw {
-
-constexpr int kT2 = 30;           // interior tile edge
-constexpr int kBox = 34;          // tile + 2 halo cells per side
-constexpr int kBP = 35;           // box pitch (odd: conflict-free column walks)
-constexpr int kFS = kBox * kBP;   // box field stride
-constexpr int kSP = 30;           // stash pitch
-constexpr int kSS = kT2 * kSP;    // stash field stride
-constexpr int kThreads2 = 256;
-
-template <int NC>
-constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
-
-template <typename T, int NC>
-constexpr size_t smem_bytes2() {
-  return sizeof(T) * (size_t)(3 * NC * kFS + stash_fields<NC>() * kSS);
-}
-
-// Component of the pass frame holding physical component k (an involution).
-template <int D, int EQ>
-__device__ constexpr int frame_comp(int k) {
-  return (EQ == HWENO_EQ_EULER && D == 1 && (k == 1 || k == 2)) ? 3 - k : k;
-}
-// Box field of frame field (d, k): d = 0 average, 1 moment along the pass
-// normal, 2 moment along the tangent.
-template <int D, int EQ, int NC>
-__device__ constexpr int frame_field(int d, int k) {
-  return (d == 0 ? 0 : (D == 0 ? d : 3 - d)) * NC + frame_comp<D, EQ>(k);
-}
-
-// Value of field f at cell (i, j), ghost cells resolved as "x sides for the
-// interior rows, then y sides for every column".
-template <typename T, int EQ, int NC>
-__device__ __forceinline__ T load_ghost2(const T* __restrict__ in, long long plane, const Grid2& G,
-                                         int f, int i, int j) {
-  const int d = f / NC, k = f % NC;
-  const GhostMap gx = ghost_map(i, G.nx, G.bc[0], G.bc[1]);
-  const GhostMap gy = ghost_map(j, G.ny, G.bc[2], G.bc[3]);
-  if (gy.fixed) return d == 0 ? (T)G.st[2 + gy.side][k] : T(0);
-  T v;
-  if (gx.fixed) {
-    v = d == 0 ? (T)G.st[gx.side][k] : T(0);
-  } else {
-    v = in[f * plane + (long long)gy.src * G.nx + gx.src];
-    if (gx.flip && mirror_negates(EQ, d, k, 0)) v = -v;
-  }
-  if (gy.flip && mirror_negates(EQ, d, k, 1)) v = -v;
-  return v;
-}
-
-// Appendix A (2D): p0 from q1..q17 of the pass frame, the linear p1..p4,
-// the smoothness indicators, the nonlinear weights and the combined
-// polynomial cu of Eq. (hweno-reconstruction-2D) in the basis
-// {1, xi, eta, xi^2, xi eta, eta^2, xi^3, xi^2 eta, xi eta^2, eta^3, xi^4,
-//  xi^3 eta, xi^2 eta^2, xi eta^3, eta^4}.
-template <typename T>
-__device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool lin, T* cu) {
-  const T q1 = q[0], q2 = q[1], q3 = q[2], q4 = q[3], q5 = q[4], q6 = q[5], q7 = q[6], q8 = q[7],
-          q9 = q[8], q10 = q[9], q11 = q[10], q12 = q[11], q13 = q[12], q14 = q[13], q15 = q[14],
-          q16 = q[15], q17 = q[16];
-  const T sc = (q1 + q3) + (q7 + q9);
-  const T cx = (q1 - q3) - (q7 - q9);
-  const T ax = (q1 - q3) + (q7 - q9);
-  const T ay = (q1 + q3) - (q7 + q9);
-  const T ex = q4 + q6, ey = q2 + q8, dxe = q6 - q4, dye = q8 - q2;
-  T c[15];
-  c[0] = (T(5) * sc - T(292) * (ex + ey) + T(4028) * q5 + T(81) * ((q11 - q10) + (q17 - q16))) *
-         T(1.0 / 2880.0);
-  c[1] = (T(2) * ax + T(19) * dxe - T(6) * (q10 + q11) + T(3) * (q12 + q13)) * T(1.0 / 24.0);
-  c[2] = (T(2) * ay + T(19) * dye + T(3) * (q14 + q15) - T(6) * (q16 + q17)) * T(1.0 / 24.0);
-  c[3] = (T(2) * ey + T(62) * ex - sc - T(124) * q5 + T(18) * (q10 - q11)) * T(1.0 / 48.0);
-  c[4] = (T(-3) * cx - T(5) * ((q12 - q13) + (q14 - q15))) * T(0.125);
-  c[5] = (T(2) * ex + T(62) * ey - sc - T(124) * q5 + T(18) * (q16 - q17)) * T(1.0 / 48.0);
-  c[6] = (T(4) * ((q10 + q11) - dxe) - ax - T(2) * (q12 + q13)) * T(0.05);
-  c[7] = ((q7 + q9 - T(2) * q8) - (q1 + q3 - T(2) * q2)) * T(0.25);
-  c[8] = ((q3 + q9 - T(2) * q6) - (q1 + q7 - T(2) * q4)) * T(0.25);
-  c[9] = (T(4) * ((q16 + q17) - dye) - ay - T(2) * (q14 + q15)) * T(0.05);
-  c[10] = (T(4) * q5 - T(2) * ex + (q11 - q10)) * T(0.25);
-  c[11] = (cx + T(2) * (q12 - q13)) * T(0.25);
-  c[12] = (sc - T(2) * (ex + ey) + T(4) * q5) * T(0.25);
-  c[13] = (cx + T(2) * (q14 - q15)) * T(0.25);
-  c[14] = (T(4) * q5 - T(2) * ey + (q17 - q16)) * T(0.25);
-  if (lin) {
-#pragma unroll
-    for (int l = 0; l < 15; ++l) cu[l] = c[l];
-    return;
-  }
-  // p1..p4 = q5 + sx xi + sy eta on S1 {W,S}, S2 {E,S}, S3 {E,N}, S4 {W,N}
-  const T dW = q5 - q4, dE = q6 - q5, dS = q5 - q2, dN = q8 - q5;
-  const T b1 = dW * dW + dS * dS, b2 = dE * dE + dS * dS, b3 = dE * dE + dN * dN, b4 = dW * dW + dN * dN;
-  const T b0 = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] + T(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
-               T(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
-               T(576) * (c[10] * c[10] + c[14] * c[14]) + T(16) * c[12] * c[12];
-  const T tau = T(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
-  const T t2 = tau * tau;
-  const T e0 = wtilde(w.g[0], t2, b0, w), e1 = wtilde(w.g[1], t2, b1, w), e2 = wtilde(w.g[2], t2, b2, w),
-          e3 = wtilde(w.g[3], t2, b3, w), e4 = wtilde(w.g[4], t2, b4, w);
-  const T inv = T(1) / ((e0 + e1) + (e2 + e3) + e4);
-  const T r = e0 * inv * w.inv_g0;
-  const T w1 = e1 * inv, w2 = e2 * inv, w3 = e3 * inv, w4 = e4 * inv;
-  const T gs = (w.g[1] + w.g[2]) + (w.g[3] + w.g[4]);
-  const T ws = (w1 + w2) + (w3 + w4);
-  cu[0] = r * (c[0] - gs * q5) + ws * q5;
-  cu[1] = r * (c[1] - ((w.g[1] + w.g[4]) * dW + (w.g[2] + w.g[3]) * dE)) + ((w1 + w4) * dW + (w2 + w3) * dE);
-  cu[2] = r * (c[2] - ((w.g[1] + w.g[2]) * dS + (w.g[3] + w.g[4]) * dN)) + ((w1 + w2) * dS + (w3 + w4) * dN);
-#pragma unroll
-  for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
-}
-
-// Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)
-// of the pass frame: u, d/dxi u, d/deta u.
-template <typename T>
-struct FacePts { T u[3], un[3], ut[3]; };
-
-template <typename T>
-__device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
-  const T s = T(0.38729833462074168852), s2 = T(0.15), s3 = s * T(0.15), s4 = T(0.0225);
-  const T A0 = (c[0] + T(0.25) * c[3] + T(0.0625) * c[10]) + sgn * (T(0.5) * c[1] + T(0.125) * c[6]);
-  const T A1 = (c[2] + T(0.25) * c[7]) + sgn * (T(0.5) * c[4] + T(0.125) * c[11]);
-  const T A2 = (c[5] + T(0.25) * c[12]) + sgn * (T(0.5) * c[8]);
-  const T A3 = c[9] + sgn * (T(0.5) * c[13]);
-  const T A4 = c[14];
-  const T B0 = (c[1] + T(0.75) * c[6]) + sgn * (c[3] + T(0.5) * c[10]);
-  const T B1 = (c[4] + T(0.75) * c[11]) + sgn * c[7];
-  const T B2 = c[8] + sgn * c[12];
-  const T B3 = c[13];
-  const T ue = A0 + A2 * s2 + A4 * s4, uo = A1 * s + A3 * s3;
-  const T ne = B0 + B2 * s2, no = B1 * s + B3 * s3;
-  const T te = A1 + T(3) * A3 * s2, to = T(2) * A2 * s + T(4) * A4 * s3;
-  o.u[0] = ue - uo; o.u[1] = A0; o.u[2] = ue + uo;
-  o.un[0] = ne - no; o.un[1] = B0; o.un[2] = ne + no;
-  o.ut[0] = te - to; o.ut[1] = A1; o.ut[2] = te + to;
-}
 
 // Lax-Friedrichs fluxes of the pass-frame x physics at one point:
 // f, f'(u) v (normal moment), f'(u) w (tangential moment).
@@ -183,10 +52,10 @@ __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, 
 // One directional pass for the lane's cell at box index bidx.  Returns the
 // Gauss-summed fluxes of the cell's low face (frame components) and the
 // limited derivative along the pass normal.  All 32 lanes must call it.
-template <typename T, int EQ, bool CHR, int D>
+template <typename T, int EQ, bool CHR, int D, bool W64>
 __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, const WeightsT<T>& w,
-                                       bool lin, T ihn, T iht, T alpha, T g, T adv, T* Fu, T* Fv, T* Fw,
-                                       T* vh) {
+                                       const WeightsT<double>& w64, bool lin, T ihn, T iht, T alpha, T g, T adv,
+                                       T* Fu, T* Fv, T* Fw, T* vh) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   constexpr int SN = D == 0 ? 1 : kBP;
   constexpr int ST = D == 0 ? kBP : 1;
@@ -222,7 +91,26 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
       for (int k = 0; k < NC; ++k) q[k][s] = x[k];
     }
 #pragma unroll
-    for (int k = 0; k < NC; ++k) recon2<T>(q[k], w, lin, cu[k]);
+    for (int k = 0; k < NC; ++k) {
+      if constexpr (W64) recon2_w64(q[k], w, w64, lin, cu[k]);
+      else recon2<T>(q[k], w, lin, cu[k]);
+    }
+  }
+  if constexpr (CHR) {
+    // R applied to the 15 coefficient vectors of the reconstructed
+    // characteristic polynomials gives the physical polynomial: every point
+    // value, derivative and v-hat below is then a physical quantity.
+    if (chr) {
+#pragma unroll
+      for (int l = 0; l < 15; ++l) {
+        T x[4], y[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = cu[k][l];
+        r2_apply<0>(e, x, y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cu[k][l] = y[k];
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < NC; ++k) { Fu[k] = T(0); Fv[k] = T(0); Fw[k] = T(0); vh[k] = T(0); }
@@ -247,19 +135,8 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
       T* Uo = side == 0 ? UR : UL;
       T* Vo = side == 0 ? VR : VL;
       T* Wo = side == 0 ? WR : WL;
-      if constexpr (CHR) {
-        if (chr) {
-          r2_apply<0>(e, u, Uo);
-          r2_apply<0>(e, un, Vo);
-          r2_apply<0>(e, ut, Wo);
-        } else {
 #pragma unroll
-          for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
-      }
+      for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
 #pragma unroll
       for (int k = 0; k < NC; ++k) { Vo[k] *= ihn; Wo[k] *= iht; }
     }
@@ -283,8 +160,8 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
   }
 }
 
-template <typename T, int EQ, bool CHR>
-__global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
+template <typename T, int EQ, bool CHR, bool W64>
+__global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k_stage2d(const Stage2Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   constexpr int NF = 3 * NC;
   extern __shared__ __align__(16) unsigned char hw_smem[];
@@ -294,7 +171,7 @@ __global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
   const T* base = static_cast<const T*>(a.base);  // aliases out at stage 3
   T* out = static_cast<T*>(a.out);
   T* __restrict__ hat = static_cast<T*>(a.hat);
-  const Grid2 G = a.grid;
+  const Grid2& G = a.grid;
   const long long plane = a.plane;
   double dt = 0.0, axd, ayd;
   if (a.stage == 0) {
@@ -310,7 +187,12 @@ __global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
   WeightsT<T> wy = wx;  // transposed frame: S2 <-> S4
   wy.g[2] = wx.g[4];
   wy.g[4] = wx.g[2];
-  const bool lin = a.wp.linear != 0;
+  const WeightsT<double> wx64 = make_weights<double>(a.wp);
+  WeightsT<double> wy64 = wx64;
+  wy64.g[2] = wx64.g[4];
+  wy64.g[4] = wx64.g[2];
+  const bool lin_all = a.wp.linear != 0;
+  const unsigned char* __restrict__ smooth = a.smooth;
   const T g = (T)a.gamma_gas;
   const T idx = (T)(1.0 / G.dx), idy = (T)(1.0 / G.dy);
   const T dyx = (T)(G.dy / G.dx), dxy = (T)(G.dx / G.dy);
@@ -345,9 +227,15 @@ __global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
     // ---- x pass: one row per warp iteration, lane l <-> cell i0-1+l ----
     for (int r = warp; r < kT2; r += nwarps) {
       if (j0 + r >= G.ny) break;
+      // learned indicator: a warp whose 32 cells are all smooth takes p0
+      bool lin = lin_all;
+      if (smooth != nullptr && !lin) {
+        const int ic = min(max(i0 - 1 + lane, 0), G.nx - 1);
+        lin = __all_sync(HW_FULL_MASK, smooth[(long long)(j0 + r) * G.nx + ic] != 0);
+      }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 0>(box, (r + 2) * kBP + lane + 1, wx, lin, idx, idy, (T)axd, g, (T)a.adv_x, Fu,
-                            Fv, Fw, vh);
+      pass2d<T, EQ, CHR, 0, W64>(box, (r + 2) * kBP + lane + 1, wx, wx64, lin, idx, idy, (T)axd, g,
+                                 (T)a.adv_x, Fu, Fv, Fw, vh);
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -372,9 +260,14 @@ __global__ void __launch_bounds__(kThreads2, 1) k_stage2d(const Stage2Args a) {
     for (int c = warp; c < kT2; c += nwarps) {
       const int i = i0 + c;
       if (i >= G.nx) break;
+      bool lin = lin_all;
+      if (smooth != nullptr && !lin) {
+        const int jc = min(max(j0 - 1 + lane, 0), G.ny - 1);
+        lin = __all_sync(HW_FULL_MASK, smooth[(long long)jc * G.nx + i] != 0);
+      }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 1>(box, (lane + 1) * kBP + c + 2, wy, lin, idy, idx, (T)ayd, g, (T)a.adv_y, Fu,
-                            Fv, Fw, vh);
+      pass2d<T, EQ, CHR, 1, W64>(box, (lane + 1) * kBP + c + 2, wy, wy64, lin, idy, idx, (T)ayd, g,
+                                 (T)a.adv_y, Fu, Fv, Fw, vh);
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -476,18 +369,18 @@ __global__ void __launch_bounds__(256) k_alpha2d(const T* __restrict__ U, long l
   }
 }
 
-template <typename T, int EQ, bool CHR>
+template <typename T, int EQ, bool CHR, bool W64>
 struct Launch2 {
   static int per_sm;  // resident CTAs per SM, 0 until prepared
   static cudaError_t prepare() {
     if (per_sm > 0) return cudaSuccess;
     constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
     constexpr size_t smem = smem_bytes2<T, NC>();
-    cudaError_t e = cudaFuncSetAttribute(k_stage2d<T, EQ, CHR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_stage2d<T, EQ, CHR, W64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR>, kThreads2, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR, W64>, kThreads2, smem);
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     per_sm = n;
@@ -503,30 +396,32 @@ struct Launch2 {
     const long long tiles = (long long)((a.grid.nx + kT2 - 1) / kT2) * ((a.grid.ny + kT2 - 1) / kT2);
     long long blocks = (long long)num_sms * per_sm;
     if (blocks > tiles) blocks = tiles;
-    k_stage2d<T, EQ, CHR><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
+    k_stage2d<T, EQ, CHR, W64><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
     return cudaGetLastError();
   }
 };
-template <typename T, int EQ, bool CHR>
-int Launch2<T, EQ, CHR>::per_sm = 0;
+template <typename T, int EQ, bool CHR, bool W64>
+int Launch2<T, EQ, CHR, W64>::per_sm = 0;
 
-template <typename T, int EQ, bool CHR>
+template <typename T, int EQ, bool CHR, bool W64 = false>
 static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st) {
-  return Launch2<T, EQ, CHR>::go(a, num_sms, st);
+  return Launch2<T, EQ, CHR, W64>::go(a, num_sms, st);
 }
 
-template <typename T>
+template <typename T, bool W64>
 static cudaError_t prep2(int equation, bool chr) {
   if (equation == HWENO_EQ_EULER)
-    return chr ? Launch2<T, HWENO_EQ_EULER, true>::prepare() : Launch2<T, HWENO_EQ_EULER, false>::prepare();
-  if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false>::prepare();
-  return Launch2<T, HWENO_EQ_ADVECTION, false>::prepare();
+    return chr ? Launch2<T, HWENO_EQ_EULER, true, W64>::prepare() : Launch2<T, HWENO_EQ_EULER, false, W64>::prepare();
+  if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false, W64>::prepare();
+  return Launch2<T, HWENO_EQ_ADVECTION, false, W64>::prepare();
 }
 
 cudaError_t prepare_stage2d(int precision, int equation, int charwise) {
   const bool chr = equation == HWENO_EQ_EULER && charwise;
   // the linear-weight path of a characteristic solver runs the same kernel
-  return precision == HWENO_FP64 ? prep2<double>(equation, chr) : prep2<float>(equation, chr);
+  if (precision == HWENO_FP64) return prep2<double, false>(equation, chr);
+  if (precision == HWENO_FP32_IND64) return prep2<float, true>(equation, chr);
+  return prep2<float, false>(equation, chr);
 }
 
 cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a, int num_sms,
@@ -537,6 +432,12 @@ cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stag
                                                : go2<double, HWENO_EQ_EULER, false>(a, num_sms, st);
     if (equation == HWENO_EQ_BURGERS) return go2<double, HWENO_EQ_BURGERS, false>(a, num_sms, st);
     return go2<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+  }
+  if (precision == HWENO_FP32_IND64) {
+    if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true, true>(a, num_sms, st)
+                                               : go2<float, HWENO_EQ_EULER, false, true>(a, num_sms, st);
+    if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st);
+    return go2<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st);
   }
   if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true>(a, num_sms, st)
                                              : go2<float, HWENO_EQ_EULER, false>(a, num_sms, st);

@@ -22,7 +22,7 @@ HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL = 0, 1, 2, 3
 HWENO_ERR_TIMEOUT, HWENO_ERR_OOM, HWENO_ERR_STATE = 4, 5, 6
 EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
-FP64, FP32 = 0, 1
+FP64, FP32, FP32_IND64 = 0, 1, 2
 DT_CFL, DT_CFL_DX53 = 0, 1
 
 # every extern "C" symbol include/hweno.h declares
@@ -33,7 +33,12 @@ EXPORTS = (
     "hweno_batch_create", "hweno_batch_destroy",
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
     "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
+    "hweno_indicator_features", "hweno_indicator_labels", "hweno_indicator_load", "hweno_indicator_off",
+    "hweno_indicator_mask", "hweno_mlp_create", "hweno_mlp_destroy", "hweno_mlp_set_params",
+    "hweno_mlp_get_params", "hweno_mlp_gradient", "hweno_mlp_train_step", "hweno_mlp_mean_loss",
+    "hweno_mlp_predict", "hweno_project",
 )
+MLP_NPARAM = 3521
 
 
 class hweno_config(C.Structure):
@@ -108,6 +113,7 @@ class HwenoError(RuntimeError):
 
 
 _lib = None
+U0_FN = C.CFUNCTYPE(None, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p)
 
 
 def load():
@@ -148,6 +154,22 @@ def load():
                                       C.POINTER(C.c_int)]
     L.hweno_batch_apply_operator.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
     L.hweno_step_1d_noalloc.argtypes = [cp, vp, vp, C.c_double, C.c_double, vp]
+    fp, ip = C.POINTER(C.c_float), C.POINTER(C.c_int)
+    L.hweno_indicator_features.argtypes = [vp, vp]
+    L.hweno_indicator_labels.argtypes = [vp, vp]
+    L.hweno_indicator_load.argtypes = [vp, fp, C.c_int, C.c_double]
+    L.hweno_indicator_off.argtypes = [vp]
+    L.hweno_indicator_mask.argtypes = [vp, vp, vp]
+    L.hweno_mlp_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+    L.hweno_mlp_destroy.argtypes = [vp]
+    L.hweno_mlp_destroy.restype = None
+    L.hweno_mlp_set_params.argtypes = [vp, fp]
+    L.hweno_mlp_get_params.argtypes = [vp, fp]
+    L.hweno_mlp_gradient.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, fp, C.POINTER(C.c_double)]
+    L.hweno_mlp_train_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_double, C.c_double, C.c_double]
+    L.hweno_mlp_mean_loss.argtypes = [vp, C.POINTER(C.c_double)]
+    L.hweno_mlp_predict.argtypes = [vp, vp, C.c_longlong, vp]
+    L.hweno_project.argtypes = [vp, U0_FN, vp, C.c_int]
     _lib = L
     return L
 
@@ -303,6 +325,93 @@ def hweno_step_1d_noalloc(cfg: Config, U_in, U_out, dt, alpha, stream=None):
     po, _ = _buf(U_out)
     _check(load().hweno_step_1d_noalloc(C.byref(c), C.c_void_p(pi), C.c_void_p(po), dt, alpha,
                                         stream if stream is not None else _current_stream()))
+
+
+def _fvec(theta):
+    a = np.ascontiguousarray(theta, dtype=np.float32)
+    assert a.size == MLP_NPARAM, a.size
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def hweno_indicator_features(h, feat_out):
+    _check(load().hweno_indicator_features(h, C.c_void_p(_buf(feat_out)[0])))
+
+
+def hweno_indicator_labels(h, dev_out):
+    _check(load().hweno_indicator_labels(h, C.c_void_p(_buf(dev_out)[0])))
+
+
+def hweno_indicator_load(h, theta, p_threshold=0.5):
+    a, pa = _fvec(theta)
+    _check(load().hweno_indicator_load(h, pa, a.size, p_threshold))
+
+
+def hweno_indicator_off(h):
+    _check(load().hweno_indicator_off(h))
+
+
+def hweno_indicator_mask(h, smooth_out=None, troubled_out=None):
+    ps = C.c_void_p(_buf(smooth_out)[0]) if smooth_out is not None else None
+    pt = C.c_void_p(_buf(troubled_out)[0]) if troubled_out is not None else None
+    _check(load().hweno_indicator_mask(h, ps, pt))
+
+
+def hweno_mlp_create(max_batch, stream=None):
+    h = C.c_void_p()
+    _check(load().hweno_mlp_create(int(max_batch), stream if stream is not None else _current_stream(),
+                                   C.byref(h)))
+    return h
+
+
+def hweno_mlp_destroy(h):
+    load().hweno_mlp_destroy(h)
+
+
+def hweno_mlp_set_params(h, theta):
+    a, pa = _fvec(theta)
+    _check(load().hweno_mlp_set_params(h, pa))
+
+
+def hweno_mlp_get_params(h):
+    out = np.zeros(MLP_NPARAM, dtype=np.float32)
+    _check(load().hweno_mlp_get_params(h, out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out
+
+
+def hweno_mlp_gradient(h, feat, dev, idx, delta, pos_weight):
+    g = np.zeros(MLP_NPARAM, dtype=np.float32)
+    loss = C.c_double()
+    _check(load().hweno_mlp_gradient(h, C.c_void_p(_buf(feat)[0]), C.c_void_p(_buf(dev)[0]),
+                                     C.c_void_p(_buf(idx)[0]), int(idx.numel()), delta, pos_weight,
+                                     g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
+    return loss.value, g
+
+
+def hweno_mlp_train_step(h, feat, dev, idx, delta, pos_weight, lr):
+    _check(load().hweno_mlp_train_step(h, C.c_void_p(_buf(feat)[0]), C.c_void_p(_buf(dev)[0]),
+                                       C.c_void_p(_buf(idx)[0]), int(idx.numel()), delta, pos_weight, lr))
+
+
+def hweno_mlp_mean_loss(h):
+    x = C.c_double()
+    _check(load().hweno_mlp_mean_loss(h, C.byref(x)))
+    return x.value
+
+
+def hweno_mlp_predict(h, feat, prob_out):
+    n = prob_out.numel()
+    _check(load().hweno_mlp_predict(h, C.c_void_p(_buf(feat)[0]), n, C.c_void_p(_buf(prob_out)[0])))
+
+
+def hweno_project(h, u0, nc, nq=6):
+    """u0(x, y) -> array (nc, n) of the conserved components at n points."""
+    def cb(n, x, y, u, ctx):
+        xs = np.ctypeslib.as_array(x, shape=(n,))
+        ys = np.ctypeslib.as_array(y, shape=(n,))
+        out = np.ctypeslib.as_array(u, shape=(n, nc))
+        out[:] = np.asarray(u0(xs, ys), dtype=np.float64).reshape(nc, n).T
+    fn = U0_FN(cb)
+    _check(load().hweno_project(h, fn, None, int(nq)))
 
 
 # ---- conveniences ----

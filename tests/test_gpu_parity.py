@@ -262,8 +262,9 @@ def test_batch_operator_and_runs():
 
 
 # ------------------------------------------------------------ FP32
+@pytest.mark.parametrize("precision", [hw.FP32, hw.FP32_IND64])
 @pytest.mark.parametrize("dim,eq", [(1, oracle.EQ_EULER), (2, oracle.EQ_EULER), (2, oracle.EQ_BURGERS)])
-def test_fp32_operator_within_fp32_conditioning(dim, eq):
+def test_fp32_operator_within_fp32_conditioning(dim, eq, precision):
     """FP32 stencil arithmetic, judged on the FP32-rounded input: every plane
     within max(2e-5, 100 x the oracle's spread under FP32 unit-roundoff input
     noise).  The derivative-equation planes are ill-conditioned (their
@@ -278,7 +279,7 @@ def test_fp32_operator_within_fp32_conditioning(dim, eq):
         f = W.euler_smooth_2d(0.0) if eq == oracle.EQ_EULER else W.sine_burgers_2d(0.0)
         U = W.cells_2d(f, 0, 2, 0, 2, N, N)
     U32 = U.astype(np.float32).astype(np.float64)
-    L, D, _, _ = _operator_pair(prob, U32, 2.5, 2.5, precision=hw.FP32)
+    L, D, _, _ = _operator_pair(prob, U32, 2.5, 2.5, precision=precision)
     Lr, Dr, sL, sD = oracle_spread(prob, U32, 2.5, 2.5, rel=2.0 ** -24)
     ok, e, tol = within_spread(L, Lr, sL, 2e-5)
     assert ok, (e, tol)
@@ -289,31 +290,32 @@ def test_fp32_operator_within_fp32_conditioning(dim, eq):
     assert plane_rel_err(L[:nc], Lr[:nc]) < 2e-3
 
 
-def test_fp32_smooth_runs_close_to_fp64_oracle():
+@pytest.mark.parametrize("precision", [hw.FP32, hw.FP32_IND64])
+def test_fp32_smooth_runs_close_to_fp64_oracle(precision):
     """Whole FP32 runs on smooth data against the FP64 oracle: the relative
     L1 difference of the cell averages stays at the FP32 rounding level."""
     N = 200
     prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=N, xlo=0, xhi=2)
     U0 = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
-    s = hw.Solver(cfg_from(prob, hw.FP32))
+    s = hw.Solver(cfg_from(prob, precision))
     s.set_state(U0)
     t, n = s.advance(0.5)
     got = s.get_state(device=False).astype(np.float64)
     ref, tr, nr = oracle.run(prob, U0, 0.5)
     assert abs(n - nr) <= 1
     rel = [np.abs(got[k] - ref[k]).mean() / np.abs(ref[k]).mean() for k in range(3)]
-    print("FP32 vs FP64 oracle, 1D Euler smooth N=200 t=0.5, relative L1 per component:", rel)
+    print(f"precision {precision} vs FP64 oracle, 1D Euler smooth N=200 t=0.5, relative L1:", rel)
     assert max(rel) < 5e-6
     N = 48
     p2 = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2, lin_w=W2D)
     V0 = W.cells_2d(W.euler_smooth_2d(0.0), 0, 2, 0, 2, N, N)
-    s2 = hw.Solver(cfg_from(p2, hw.FP32))
+    s2 = hw.Solver(cfg_from(p2, precision))
     s2.set_state(V0)
     s2.advance(0.25)
     g2 = s2.get_state(device=False).astype(np.float64)
     r2, _, _ = oracle.run(p2, V0, 0.25)
     rel2 = [np.abs(g2[k] - r2[k]).mean() / np.abs(r2[k]).mean() for k in range(4)]
-    print("FP32 vs FP64 oracle, 2D Euler smooth 48^2 t=0.25, relative L1 per component:", rel2)
+    print(f"precision {precision} vs FP64 oracle, 2D Euler smooth 48^2 t=0.25, relative L1:", rel2)
     assert max(rel2) < 5e-6
 
 
@@ -329,3 +331,36 @@ def test_nonphysical_state_reported():
         s.set_state(U)
         s.advance(0.1)
     assert ei.value.status == hw.HWENO_ERR_NONPHYSICAL
+
+
+def test_fp32_ind64_shock_run_l1():
+    """Mixed precision through shocks (four-quadrant problem) vs the oracle:
+    relative L1 of every component within 1e-5."""
+    N = 48
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, lin_w=W2D, bc=(oracle.BC_OUTFLOW,) * 4)
+    U0 = W.quadrant_2d(W.quadrant_states(2024), 0.5, 0.5, 0, 1, 0, 1, N, N)
+    s = hw.Solver(cfg_from(prob, hw.FP32_IND64))
+    s.set_state(U0)
+    s.advance(0.05)
+    got = s.get_state(device=False).astype(np.float64)
+    ref, _, _ = oracle.run(prob, U0, 0.05)
+    for k in range(4):
+        assert np.abs(got[k] - ref[k]).mean() < 1e-5 * np.abs(ref[k]).mean()
+
+
+def test_project_matches_input_generator():
+    """hweno_project (host Gauss-Legendre of a u0 callback) gives the cell
+    averages and derivative moments the shared input generator computes."""
+    N = 24
+    cfg = hw.Config(dim=2, nx=N, ny=N + 3, xlo=0, xhi=2, ylo=-1, yhi=1, equation=hw.EQ_EULER, lin_w=W2D)
+    s = hw.Solver(cfg)
+    f = W.euler_smooth_2d(0.3)
+    hw.hweno_project(s.h, f, nc=4, nq=6)
+    got = s.get_state(device=False)
+    ref = W.cells_2d(f, 0, 2, -1, 1, N, N + 3, nq=6)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    c1 = hw.Config(dim=1, nx=50, xlo=0, xhi=2, equation=hw.EQ_BURGERS)
+    s1 = hw.Solver(c1)
+    f1 = W.sine_burgers_1d(0.1)
+    hw.hweno_project(s1.h, lambda x, y: f1(x), nc=1, nq=5)
+    np.testing.assert_allclose(s1.get_state(device=False), W.cells_1d(f1, 0, 2, 50, nq=5), rtol=0, atol=1e-13)
