@@ -208,6 +208,7 @@ def time_arm(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, theta=Non
     if theta is not None:
         hw.hweno_indicator_load(s.h, theta, 0.5)
     s.set_state(U0_dev)
+    tune_ms, shape = hw.hweno_autotune(s.h, reps=2)
     s.advance(1e30, max_steps=warmup)
     s.set_state(U0_dev)       # the timed steps start from the workload's initial state
     stream = torch.cuda.ExternalStream(s.stream)
@@ -233,7 +234,8 @@ def time_arm(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, theta=Non
         smooth = float(sm.float().mean().item())
     s.close()
     return {"ms": ms, "stage_ms_avg": stage_ms / max(stage_n, 1), "stage_launches": stage_n,
-            "launches": launches, "clocks": clk.summary(), "rho": rho, "t": t, "smooth_fraction": smooth}
+            "launches": launches, "clocks": clk.summary(), "rho": rho, "t": t, "smooth_fraction": smooth,
+            "launch_shape": {"persistent_grid": bool(shape[2])}}
 
 
 def train_indicator(verbose=False):
@@ -305,6 +307,7 @@ def run_batch1d(args, hw, torch, rank, local):
         b = hw.Batch(cfgs)
         U = torch.from_numpy(b.pack([B.instance(k) for k in range(b.n)])).cuda()
         b.set_state(U)
+        tune_ms, shape = hw.hweno_batch_autotune(b.h, reps=3)
         b.advance(1e30, max_steps=args.warmup)
         b.set_state(U)
         stream = torch.cuda.ExternalStream(b.stream)
@@ -319,7 +322,7 @@ def run_batch1d(args, hw, torch, rank, local):
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
         out[name] = {"value": b.total * 3 * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps,
-                     "cells": int(b.total)}
+                     "cells": int(b.total), "launch_shape": {"warps_per_block": shape[0], "blocks_per_sm": shape[1]}}
         b.close()
     if rank == 0:
         line = {"metric": METRIC, "value": out["fp64"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -448,7 +451,8 @@ def main():
                "dtype": {hw.FP64: "f64", hw.FP32: "f32", hw.FP32_IND64: "f32 (f64 indicators/weights)"}[prec],
                "roofline": roofline(r, prec, fp32_peak if prec == hw.FP32 else fp64_peak,
                                     learned=r["smooth_fraction"] is not None),
-               "hbm": hbm(r, 8 if prec == hw.FP64 else 4), "clocks": r["clocks"], "gpu_launches": r["launches"]}
+               "hbm": hbm(r, 8 if prec == hw.FP64 else 4), "clocks": r["clocks"], "gpu_launches": r["launches"],
+               "launch_shape": r["launch_shape"]}
         if ref_rho is not None:
             out["l1_rho_vs_fp64"] = float((r["rho"] - ref_rho).abs().mean() / ref_rho.abs().mean())
             if "fp64" in arms:

@@ -141,6 +141,13 @@ hweno_status hweno_set_state(hweno_solver* s, const void* U, int on_device);
 /* Copy the current state out (same layout); synchronises if !on_device. */
 hweno_status hweno_get_state(hweno_solver* s, void* U, int on_device);
 
+/* Simulation time of the current state and the steps taken by the last
+ * advance (synchronises); set_time restores a checkpoint's time after
+ * hweno_set_state (which resets it to 0).  The wave speeds are a function of
+ * the state, so set_state + set_time resumes a run bit for bit. */
+hweno_status hweno_get_time(hweno_solver* s, double* t, int* steps);
+hweno_status hweno_set_time(hweno_solver* s, double t);
+
 /* Max spectral radius over the cell averages of the current state
  * (alpha of the global Lax-Friedrichs flux, Sec. 2.1 and 2.2).  Synchronises. */
 hweno_status hweno_alpha(hweno_solver* s, double* alpha_x, double* alpha_y);
@@ -181,6 +188,15 @@ hweno_status hweno_profile(hweno_solver* s, double* stage_ms, long long* stage_l
  * short probe kernel (milliseconds); synchronises the device. */
 hweno_status hweno_peak_fma(int precision, double* flops_per_second);
 
+/* Autotuner: time the candidate launch shapes of the stage kernel on the
+ * current state (reps operator applications each, CUDA events) and keep the
+ * fastest for every later launch.  1D: warps per block {2, 4, 8} x resident
+ * blocks per SM {4, 8, 16, 32}; 2D: persistent grid (tiles looped over one
+ * CTA per SM slot) or one CTA per tile.  best_ms (may be NULL) receives the
+ * winner's time per launch, shape_out[3] (may be NULL) the winner (warps,
+ * blocks per SM, persistent).  Allocates and frees two temporary buffers. */
+hweno_status hweno_autotune(hweno_solver* s, int reps, double* best_ms, int* shape_out);
+
 /* ---- Batches of independent 1D problems of uneven sizes (one launch per
  * stage for all instances, per-instance alpha, dt, time and done flag). ---- */
 /* cfgs[n] are 1D configs with the same equation, precision and weights. */
@@ -199,6 +215,8 @@ hweno_status hweno_batch_get_state(hweno_batch* b, void* U, int on_device);
  * instance results. */
 hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_steps,
                                  double* t_out, int* steps_out);
+/* The autotuner of hweno_autotune for a batch (all instances at once). */
+hweno_status hweno_batch_autotune(hweno_batch* b, int reps, double* best_ms, int* shape_out);
 /* Apply the operator to every instance with per-instance alpha (host array):
  * L_out [nf][total], dhat_out [nc][total] (device buffers). */
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,

@@ -117,6 +117,7 @@ struct Engine {
   hw::WeightParams wp{};
   cudaGraphExec_t gexec = nullptr;
   bool has_state = false;
+  hw::LaunchShape shape;          // chosen by the autotuner
   // opt-in timing of every stage launch with CUDA events (direct launches)
   bool prof = false;
   std::vector<cudaEvent_t> pev;   // 2 per stage launch of one poll window
@@ -248,7 +249,7 @@ struct Engine {
       a.inst = inst_d; a.tasks = tasks_d; a.ntasks = ntasks; a.total = cells;
       a.ctl = c; a.alpha_op = alpha_op; a.stage = s;
       a.gamma_gas = cfg.gamma_gas; a.adv = cfg.adv_x; a.wp = wp;
-      HW_CK(hw::launch_stage1d(prec, cfg.equation, cfg.charwise, a, num_sms, own));
+      HW_CK(hw::launch_stage1d(prec, cfg.equation, cfg.charwise, a, num_sms, own, shape));
     } else {
       hw::Stage2Args a{};
       a.in = in; a.base = S; a.out = out; a.hat = hat;
@@ -256,7 +257,7 @@ struct Engine {
       a.gamma_gas = cfg.gamma_gas; a.adv_x = cfg.adv_x; a.adv_y = cfg.adv_y; a.wp = wp;
       a.plane = cells;
       a.smooth = learned && s > 0 ? smooth : nullptr;
-      HW_CK(hw::launch_stage2d(prec, cfg.equation, cfg.charwise, a, num_sms, own));
+      HW_CK(hw::launch_stage2d(prec, cfg.equation, cfg.charwise, a, num_sms, own, shape));
     }
     return HWENO_OK;
   }
@@ -486,6 +487,64 @@ struct Engine {
     learned = true;
     drop_graph();
     return HWENO_OK;
+  }
+
+  // Time every candidate launch shape on the current state (operator mode,
+  // reps launches each, CUDA events) and keep the fastest.
+  hweno_status autotune(int reps, double* best_ms) {
+    if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
+    if (reps < 1 || reps > 1000) return fail(HWENO_ERR_ARG, "reps must lie in [1, 1000]");
+    HW_TRY(enter());
+    std::vector<hw::LaunchShape> cand;
+    if (dim == 1) {
+      for (int wpb : {2, 4, 8})
+        for (int bps : {4, 8, 16, 32}) {
+          hw::LaunchShape s;
+          s.warps1d = wpb;
+          s.blocks_per_sm1d = bps;
+          cand.push_back(s);
+        }
+    } else {
+      for (int p : {1, 0}) {
+        hw::LaunchShape s;
+        s.persistent2d = p;
+        cand.push_back(s);
+      }
+    }
+    void *L = nullptr, *D = nullptr;
+    HW_CK(cudaMalloc(&L, (size_t)cells * esz * nf));
+    HW_CK(cudaMalloc(&D, (size_t)cells * esz * nd));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HW_CK(cudaEventCreate(&e0));
+    HW_CK(cudaEventCreate(&e1));
+    std::vector<double> a0(n_inst, 1.0);
+    if (dim == 1) HW_CK(cudaMemcpy(alpha_op, a0.data(), sizeof(double) * n_inst, cudaMemcpyHostToDevice));
+    const hw::LaunchShape keep = shape;
+    double best = 1e300;
+    hw::LaunchShape pick = keep;
+    hweno_status st = HWENO_OK;
+    for (const hw::LaunchShape& c : cand) {
+      shape = c;
+      st = stage(0, S, L, ctl, 1.0, 1.0, D);  // warm-up
+      if (st != HWENO_OK) break;
+      cudaEventRecord(e0, own);
+      for (int r = 0; r < reps && st == HWENO_OK; ++r) st = stage(0, S, L, ctl, 1.0, 1.0, D);
+      cudaEventRecord(e1, own);
+      if (st != HWENO_OK) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = c; }
+    }
+    shape = st == HWENO_OK ? pick : keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(L);
+    cudaFree(D);
+    if (st != HWENO_OK) return st;
+    if (best_ms) *best_ms = best / reps;
+    drop_graph();
+    return leave();
   }
 
   void drop_graph() {
@@ -839,6 +898,51 @@ hweno_status hweno_mlp_predict(hweno_mlp* m, const float* feat, long long n, flo
 }
 
 }  // extern "C"
+
+extern "C" hweno_status hweno_get_time(hweno_solver* s, double* t, int* steps) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  if (!s->e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(s->e.enter());
+  HW_TRY(s->e.read_ctl());
+  if (t) *t = s->e.ctl_host[0].t;
+  if (steps) *steps = s->e.ctl_host[0].steps;
+  return s->e.leave();
+}
+
+extern "C" hweno_status hweno_set_time(hweno_solver* s, double t) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  if (!std::isfinite(t) || t < 0.0) return fail(HWENO_ERR_ARG, "t must be finite and non-negative");
+  Engine& e = s->e;
+  if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(e.enter());
+  HW_TRY(e.read_ctl());
+  e.ctl_host[0].t = t;
+  HW_CK(cudaMemcpyAsync(e.ctl, e.ctl_host, sizeof(hw::Ctl), cudaMemcpyHostToDevice, e.own));
+  HW_CK(cudaStreamSynchronize(e.own));
+  return e.leave();
+}
+
+extern "C" hweno_status hweno_autotune(hweno_solver* s, int reps, double* best_ms, int* shape_out) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  HW_TRY(s->e.autotune(reps, best_ms));
+  if (shape_out) {
+    shape_out[0] = s->e.shape.warps1d;
+    shape_out[1] = s->e.shape.blocks_per_sm1d;
+    shape_out[2] = s->e.shape.persistent2d;
+  }
+  return HWENO_OK;
+}
+
+extern "C" hweno_status hweno_batch_autotune(hweno_batch* b, int reps, double* best_ms, int* shape_out) {
+  if (!b) return fail(HWENO_ERR_ARG, "batch is NULL");
+  HW_TRY(b->e.autotune(reps, best_ms));
+  if (shape_out) {
+    shape_out[0] = b->e.shape.warps1d;
+    shape_out[1] = b->e.shape.blocks_per_sm1d;
+    shape_out[2] = b->e.shape.persistent2d;
+  }
+  return HWENO_OK;
+}
 
 extern "C" hweno_status hweno_project(hweno_solver* s, hweno_u0_fn u0, void* ctx, int nq) {
   if (!s || !u0) return fail(HWENO_ERR_ARG, "solver or u0 is NULL");

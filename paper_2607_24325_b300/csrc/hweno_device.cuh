@@ -287,14 +287,14 @@ __device__ __forceinline__ void euler2_flux(const T* U, const T* V, const T* Wv,
   }
 }
 
-// Spectral radius |u_n| + c (Euler) at a cell average; NaN if non-physical.
+// Spectral radius |u_n| + c (Euler) at a cell average, in the state's own
+// precision (it only sets alpha and dt); NaN if non-physical.
 template <typename T>
 __device__ __forceinline__ double euler_radius(T r, T mn, T ekin2, T E, T g) {
   // ekin2 = |m|^2 (sum of squared momenta)
-  const double rr = (double)r;
-  const double p = ((double)g - 1.0) * ((double)E - 0.5 * (double)ekin2 / rr);
-  if (!(rr > 0.0) || !(p > 0.0)) return __longlong_as_double(0x7ff8000000000000LL);
-  return fabs((double)mn / rr) + sqrt((double)g * p / rr);
+  const T p = (g - T(1)) * (E - T(0.5) * ekin2 / r);
+  if (!(r > T(0)) || !(p > T(0))) return __longlong_as_double(0x7ff8000000000000LL);
+  return (double)(fabs_t(mn / r) + sqrt(g * p / r));
 }
 
 // Running max of non-negative doubles through their bit patterns (exact,

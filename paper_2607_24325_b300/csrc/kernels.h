@@ -59,13 +59,22 @@ constexpr int kMlpParams = 3521;
 
 constexpr int kTile1 = 30;   // interior cells per warp task (32 lanes - 2 ring cells)
 
+// Launch shapes chosen by the autotuner: 1D warps per block (1..8) and a cap
+// on resident blocks per SM for the persistent grid; 2D persistent grid
+// (one CTA per SM slot, tiles looped) or one CTA per tile.
+struct LaunchShape {
+  int warps1d = 4;
+  int blocks_per_sm1d = 16;
+  int persistent2d = 1;
+};
+
 cudaError_t launch_stage1d(int precision, int equation, int charwise, const Stage1Args& a,
-                           int num_sms, cudaStream_t st);
+                           int num_sms, cudaStream_t st, const LaunchShape& shape = LaunchShape());
 cudaError_t launch_alpha1d(int precision, int equation, const void* U, long long total,
                            const Inst1* inst, const int2* tasks, int ntasks, double gamma_gas,
                            double adv, Ctl* ctl, int num_sms, cudaStream_t st);
 cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a,
-                           int num_sms, cudaStream_t st);
+                           int num_sms, cudaStream_t st, const LaunchShape& shape = LaunchShape());
 cudaError_t prepare_stage2d(int precision, int equation, int charwise);
 cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane,
                            double gamma_gas, double adv_x, double adv_y, Ctl* ctl, int num_sms,

@@ -69,7 +69,7 @@ __device__ __forceinline__ void lf_flux1(const T* um, const T* up, const T* vm, 
 }
 
 template <typename T, int EQ, bool CHR, bool W64>
-__global__ void __launch_bounds__(128) k_stage1d(const Stage1Args a) {
+__global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 3 : 1;
   const T* __restrict__ in = static_cast<const T*>(a.in);
   const T* base = static_cast<const T*>(a.base);  // aliases out at stage 3
@@ -212,10 +212,10 @@ __global__ void __launch_bounds__(128) k_alpha1d(const T* __restrict__ U, long l
 }
 
 template <typename T, int EQ, bool CHR, bool W64 = false>
-static cudaError_t go1(const Stage1Args& a, int num_sms, cudaStream_t st) {
-  const int warps = 4;
+static cudaError_t go1(const Stage1Args& a, int num_sms, cudaStream_t st, const LaunchShape& sh) {
+  const int warps = sh.warps1d < 1 ? 1 : (sh.warps1d > 8 ? 8 : sh.warps1d);
   long long blocks = (a.ntasks + warps - 1) / warps;
-  const long long cap = (long long)num_sms * 16;
+  const long long cap = (long long)num_sms * (sh.blocks_per_sm1d < 1 ? 1 : sh.blocks_per_sm1d);
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   k_stage1d<T, EQ, CHR, W64><<<(unsigned)blocks, 32 * warps, 0, st>>>(a);
@@ -223,25 +223,25 @@ static cudaError_t go1(const Stage1Args& a, int num_sms, cudaStream_t st) {
 }
 
 cudaError_t launch_stage1d(int precision, int equation, int charwise, const Stage1Args& a,
-                           int num_sms, cudaStream_t st) {
+                           int num_sms, cudaStream_t st, const LaunchShape& sh) {
   if (a.ntasks <= 0) return cudaSuccess;
   const bool chr = equation == HWENO_EQ_EULER && charwise;
   if (precision == HWENO_FP64) {
-    if (equation == HWENO_EQ_EULER) return chr ? go1<double, HWENO_EQ_EULER, true>(a, num_sms, st)
-                                               : go1<double, HWENO_EQ_EULER, false>(a, num_sms, st);
-    if (equation == HWENO_EQ_BURGERS) return go1<double, HWENO_EQ_BURGERS, false>(a, num_sms, st);
-    return go1<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+    if (equation == HWENO_EQ_EULER) return chr ? go1<double, HWENO_EQ_EULER, true>(a, num_sms, st, sh)
+                                               : go1<double, HWENO_EQ_EULER, false>(a, num_sms, st, sh);
+    if (equation == HWENO_EQ_BURGERS) return go1<double, HWENO_EQ_BURGERS, false>(a, num_sms, st, sh);
+    return go1<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st, sh);
   }
   if (precision == HWENO_FP32_IND64) {
-    if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true, true>(a, num_sms, st)
-                                               : go1<float, HWENO_EQ_EULER, false, true>(a, num_sms, st);
-    if (equation == HWENO_EQ_BURGERS) return go1<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st);
-    return go1<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st);
+    if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true, true>(a, num_sms, st, sh)
+                                               : go1<float, HWENO_EQ_EULER, false, true>(a, num_sms, st, sh);
+    if (equation == HWENO_EQ_BURGERS) return go1<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st, sh);
+    return go1<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st, sh);
   }
-  if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true>(a, num_sms, st)
-                                             : go1<float, HWENO_EQ_EULER, false>(a, num_sms, st);
-  if (equation == HWENO_EQ_BURGERS) return go1<float, HWENO_EQ_BURGERS, false>(a, num_sms, st);
-  return go1<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+  if (equation == HWENO_EQ_EULER) return chr ? go1<float, HWENO_EQ_EULER, true>(a, num_sms, st, sh)
+                                             : go1<float, HWENO_EQ_EULER, false>(a, num_sms, st, sh);
+  if (equation == HWENO_EQ_BURGERS) return go1<float, HWENO_EQ_BURGERS, false>(a, num_sms, st, sh);
+  return go1<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st, sh);
 }
 
 cudaError_t launch_alpha1d(int precision, int equation, const void* U, long long total,

@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
   const T idx = (T)(1.0 / G.dx), idy = (T)(1.0 / G.dy);
   const T dyx = (T)(G.dy / G.dx), dxy = (T)(G.dx / G.dy);
   const T tdt = (T)dt;
+  // converted once: a double -> float conversion runs on the narrow FP64 pipe
+  const T ax_t = (T)axd, ay_t = (T)ayd, advx_t = (T)a.adv_x, advy_t = (T)a.adv_y;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int tiles_x = (G.nx + kT2 - 1) / kT2;
@@ -234,8 +236,8 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
         lin = __all_sync(HW_FULL_MASK, smooth[(long long)(j0 + r) * G.nx + ic] != 0);
       }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 0, W64>(box, (r + 2) * kBP + lane + 1, wx, wx64, lin, idx, idy, (T)axd, g,
-                                 (T)a.adv_x, Fu, Fv, Fw, vh);
+      pass2d<T, EQ, CHR, 0, W64>(box, (r + 2) * kBP + lane + 1, wx, wx64, lin, idx, idy, ax_t, g, advx_t, Fu,
+                                 Fv, Fw, vh);
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -266,8 +268,8 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
         lin = __all_sync(HW_FULL_MASK, smooth[(long long)jc * G.nx + i] != 0);
       }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 1, W64>(box, (lane + 1) * kBP + c + 2, wy, wy64, lin, idy, idx, (T)ayd, g,
-                                 (T)a.adv_y, Fu, Fv, Fw, vh);
+      pass2d<T, EQ, CHR, 1, W64>(box, (lane + 1) * kBP + c + 2, wy, wy64, lin, idy, idx, ay_t, g, advy_t, Fu,
+                                 Fv, Fw, vh);
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -386,7 +388,7 @@ struct Launch2 {
     per_sm = n;
     return cudaSuccess;
   }
-  static cudaError_t go(const Stage2Args& a, int num_sms, cudaStream_t st) {
+  static cudaError_t go(const Stage2Args& a, int num_sms, cudaStream_t st, const LaunchShape& sh) {
     constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
     constexpr size_t smem = smem_bytes2<T, NC>();
     if (per_sm == 0) {
@@ -394,7 +396,7 @@ struct Launch2 {
       if (e != cudaSuccess) return e;
     }
     const long long tiles = (long long)((a.grid.nx + kT2 - 1) / kT2) * ((a.grid.ny + kT2 - 1) / kT2);
-    long long blocks = (long long)num_sms * per_sm;
+    long long blocks = sh.persistent2d ? (long long)num_sms * per_sm : tiles;
     if (blocks > tiles) blocks = tiles;
     k_stage2d<T, EQ, CHR, W64><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
     return cudaGetLastError();
@@ -404,8 +406,8 @@ template <typename T, int EQ, bool CHR, bool W64>
 int Launch2<T, EQ, CHR, W64>::per_sm = 0;
 
 template <typename T, int EQ, bool CHR, bool W64 = false>
-static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st) {
-  return Launch2<T, EQ, CHR, W64>::go(a, num_sms, st);
+static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st, const LaunchShape& sh) {
+  return Launch2<T, EQ, CHR, W64>::go(a, num_sms, st, sh);
 }
 
 template <typename T, bool W64>
@@ -425,24 +427,24 @@ cudaError_t prepare_stage2d(int precision, int equation, int charwise) {
 }
 
 cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a, int num_sms,
-                           cudaStream_t st) {
+                           cudaStream_t st, const LaunchShape& sh) {
   const bool chr = equation == HWENO_EQ_EULER && charwise;
   if (precision == HWENO_FP64) {
-    if (equation == HWENO_EQ_EULER) return chr ? go2<double, HWENO_EQ_EULER, true>(a, num_sms, st)
-                                               : go2<double, HWENO_EQ_EULER, false>(a, num_sms, st);
-    if (equation == HWENO_EQ_BURGERS) return go2<double, HWENO_EQ_BURGERS, false>(a, num_sms, st);
-    return go2<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+    if (equation == HWENO_EQ_EULER) return chr ? go2<double, HWENO_EQ_EULER, true>(a, num_sms, st, sh)
+                                               : go2<double, HWENO_EQ_EULER, false>(a, num_sms, st, sh);
+    if (equation == HWENO_EQ_BURGERS) return go2<double, HWENO_EQ_BURGERS, false>(a, num_sms, st, sh);
+    return go2<double, HWENO_EQ_ADVECTION, false>(a, num_sms, st, sh);
   }
   if (precision == HWENO_FP32_IND64) {
-    if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true, true>(a, num_sms, st)
-                                               : go2<float, HWENO_EQ_EULER, false, true>(a, num_sms, st);
-    if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st);
-    return go2<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st);
+    if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true, true>(a, num_sms, st, sh)
+                                               : go2<float, HWENO_EQ_EULER, false, true>(a, num_sms, st, sh);
+    if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false, true>(a, num_sms, st, sh);
+    return go2<float, HWENO_EQ_ADVECTION, false, true>(a, num_sms, st, sh);
   }
-  if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true>(a, num_sms, st)
-                                             : go2<float, HWENO_EQ_EULER, false>(a, num_sms, st);
-  if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false>(a, num_sms, st);
-  return go2<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st);
+  if (equation == HWENO_EQ_EULER) return chr ? go2<float, HWENO_EQ_EULER, true>(a, num_sms, st, sh)
+                                             : go2<float, HWENO_EQ_EULER, false>(a, num_sms, st, sh);
+  if (equation == HWENO_EQ_BURGERS) return go2<float, HWENO_EQ_BURGERS, false>(a, num_sms, st, sh);
+  return go2<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st, sh);
 }
 
 cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane, double gamma_gas,

@@ -36,7 +36,8 @@ EXPORTS = (
     "hweno_indicator_features", "hweno_indicator_labels", "hweno_indicator_load", "hweno_indicator_off",
     "hweno_indicator_mask", "hweno_mlp_create", "hweno_mlp_destroy", "hweno_mlp_set_params",
     "hweno_mlp_get_params", "hweno_mlp_gradient", "hweno_mlp_train_step", "hweno_mlp_mean_loss",
-    "hweno_mlp_predict", "hweno_project",
+    "hweno_mlp_predict", "hweno_project", "hweno_autotune", "hweno_batch_autotune",
+    "hweno_get_time", "hweno_set_time",
 )
 MLP_NPARAM = 3521
 
@@ -170,6 +171,10 @@ def load():
     L.hweno_mlp_mean_loss.argtypes = [vp, C.POINTER(C.c_double)]
     L.hweno_mlp_predict.argtypes = [vp, vp, C.c_longlong, vp]
     L.hweno_project.argtypes = [vp, U0_FN, vp, C.c_int]
+    L.hweno_get_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.hweno_set_time.argtypes = [vp, C.c_double]
+    L.hweno_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.hweno_batch_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
     _lib = L
     return L
 
@@ -414,6 +419,30 @@ def hweno_project(h, u0, nc, nq=6):
     _check(load().hweno_project(h, fn, None, int(nq)))
 
 
+def hweno_get_time(h):
+    t, n = C.c_double(), C.c_int()
+    _check(load().hweno_get_time(h, C.byref(t), C.byref(n)))
+    return t.value, n.value
+
+
+def hweno_set_time(h, t):
+    _check(load().hweno_set_time(h, float(t)))
+
+
+def hweno_autotune(h, reps=3):
+    ms = C.c_double()
+    shp = (C.c_int * 3)()
+    _check(load().hweno_autotune(h, int(reps), C.byref(ms), shp))
+    return ms.value, tuple(shp)
+
+
+def hweno_batch_autotune(h, reps=3):
+    ms = C.c_double()
+    shp = (C.c_int * 3)()
+    _check(load().hweno_batch_autotune(h, int(reps), C.byref(ms), shp))
+    return ms.value, tuple(shp)
+
+
 # ---- conveniences ----
 class Solver:
     """One grid.  State tensors are [nf, ny, nx] (2D) or [nf, nx] (1D)."""
@@ -475,6 +504,21 @@ class Solver:
 
     def advance(self, t_final, max_steps=2**31 - 1):
         return hweno_advance(self.h, t_final, max_steps)
+
+    def save(self, path: str):
+        """Checkpoint: state, time and the config's fields to an .npz file."""
+        import dataclasses
+        t, _ = hweno_get_time(self.h)
+        cfg = {k: np.asarray(v) for k, v in dataclasses.asdict(self.cfg).items()}
+        np.savez(path, U=self.get_state(device=False), t=np.float64(t), **{"cfg_" + k: v for k, v in cfg.items()})
+
+    def load(self, path: str):
+        """Resume from save(): same grid and scheme required."""
+        z = np.load(path)
+        if tuple(z["U"].shape) != self.shape:
+            raise ValueError("checkpoint state shape does not match this solver")
+        self.set_state(np.ascontiguousarray(z["U"]))
+        hweno_set_time(self.h, float(z["t"]))
 
     def set_profiling(self, enable: bool = True):
         hweno_set_profiling(self.h, enable)

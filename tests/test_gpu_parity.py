@@ -364,3 +364,47 @@ def test_project_matches_input_generator():
     f1 = W.sine_burgers_1d(0.1)
     hw.hweno_project(s1.h, lambda x, y: f1(x), nc=1, nq=5)
     np.testing.assert_allclose(s1.get_state(device=False), W.cells_1d(f1, 0, 2, 50, nq=5), rtol=0, atol=1e-13)
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes launch shapes: operator results before and
+    after tuning are identical (same arithmetic per cell), 1D batch and 2D."""
+    B = W.riemann_batch_1d(n=5, seed=3, nmin=40, nmax=400)
+    cfgs = [hw.Config(dim=1, nx=int(B.sizes[k]), equation=hw.EQ_EULER, bc=(hw.BC_OUTFLOW,) * 4) for k in range(5)]
+    b = hw.Batch(cfgs)
+    b.set_state(torch.from_numpy(b.pack([B.instance(k) for k in range(5)])).cuda())
+    L0, D0 = b.apply_operator([1.5] * 5)
+    ms, shape = hw.hweno_batch_autotune(b.h, reps=2)
+    assert ms > 0 and shape[0] in (2, 4, 8) and shape[1] in (4, 8, 16, 32)
+    L1, D1 = b.apply_operator([1.5] * 5)
+    assert torch.equal(L0, L1) and torch.equal(D0, D1)
+    N = 70
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, lin_w=W2D, bc=(1, 1, 1, 1))
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(W.quadrant_2d(W.quadrant_states(5), 0.5, 0.5, 0, 1, 0, 1, N, N))
+    La, Da = s.apply_operator(2.0, 2.0)
+    ms, shape = hw.hweno_autotune(s.h, reps=2)
+    assert shape[2] in (0, 1)
+    Lb, Db = s.apply_operator(2.0, 2.0)
+    assert torch.equal(La, Lb) and torch.equal(Da, Db)
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    """Run 2N steps == run N, save, load into a fresh solver, run N (bitwise)."""
+    N = 64
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, lin_w=W2D, bc=(1, 1, 1, 1))
+    U0 = W.quadrant_2d(W.quadrant_states(2024), 0.5, 0.5, 0, 1, 0, 1, N, N)
+    a = hw.Solver(cfg_from(prob))
+    a.set_state(U0)
+    a.advance(1e9, max_steps=20)
+    ta, _ = hw.hweno_get_time(a.h)
+    b = hw.Solver(cfg_from(prob))
+    b.set_state(U0)
+    b.advance(1e9, max_steps=10)
+    b.save(str(tmp_path / "ck.npz"))
+    c = hw.Solver(cfg_from(prob))
+    c.load(str(tmp_path / "ck.npz"))
+    c.advance(1e9, max_steps=10)
+    tc, _ = hw.hweno_get_time(c.h)
+    assert ta == tc
+    assert np.array_equal(a.get_state(device=False), c.get_state(device=False))
