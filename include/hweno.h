@@ -188,6 +188,18 @@ hweno_status hweno_profile(hweno_solver* s, double* stage_ms, long long* stage_l
  * short probe kernel (milliseconds); synchronises the device. */
 hweno_status hweno_peak_fma(int precision, double* flops_per_second);
 
+/* Self-check of the integer-ALU conversions of the mixed-precision path
+ * (HWENO_FP32_IND64 widens its FP32 inputs to FP64 and narrows the FP64
+ * weights back without the FP64 pipe).  Not part of the paper's method: a
+ * diagnostic that exposes those two routines.  For i < n (device pointers,
+ * caller-owned): wide_out[i] = f_in[i] widened to FP64 (exact),
+ * narrow_out[i] = d_in[i] rounded to FP32 (to nearest, ties to even), both
+ * as IEEE 754 conversions must give.  Launches on the legacy default stream
+ * and synchronises the device.  HWENO_ERR_ARG for n < 0 or a null pointer
+ * with n > 0. */
+hweno_status hweno_selftest_convert(const float* f_in, double* wide_out, const double* d_in, float* narrow_out,
+                                    int n);
+
 /* Autotuner: time the candidate launch shapes of the stage kernel on the
  * current state (reps operator applications each, CUDA events) and keep the
  * fastest for every later launch.  1D: warps per block {2, 4, 8} x resident

@@ -46,6 +46,48 @@ __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double div_t(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+// Square root in the argument's own precision (an unqualified sqrt of a
+// float would promote to the FP64 pipe).
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+
+// Exact FP32 -> FP64 widening on the integer ALU, from the IEEE 754
+// binary32 / binary64 encodings: the exponent is re-biased by 1023 - 127 =
+// 896 and the 23 fraction bits move to the top of the 52-bit fraction.
+// Zero keeps its sign; subnormals, infinities and NaN (exponent field 0 with
+// a nonzero fraction, or 255) take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned mag = u & 0x7fffffffu;
+  if ((mag >> 23) - 1u >= 254u) {
+    if (mag == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    return (double)x;
+  }
+  const unsigned hi = (u & 0x80000000u) | ((mag >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// FP64 -> FP32 with round-to-nearest-even on the integer ALU: the 29 dropped
+// fraction bits decide the rounding, a carry out of the fraction moves into
+// the exponent.  Values whose binary32 image is not a normal number
+// (exponent field outside 897..1150) take the hardware conversion.
+__device__ __forceinline__ float narrow_f64(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u > 253u) return (float)x;
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1fffffffu;
+  unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | frac;
+  bits += (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
+  return __uint_as_float(bits);
+}
+
+// Input conversion of the coefficient maps: identity, or the exact widening.
+template <typename TC, typename TQ>
+__device__ __forceinline__ TC to_tc(TQ x) {
+  if constexpr (sizeof(TC) == 8 && sizeof(TQ) == 4) return widen_f32(x);
+  else return (TC)x;
+}
 
 // Nonlinear weights of Eq. (nonlinear-weights) / (nonlinear-weights-2D) for
 // one target polynomial and NL linear ones: given beta_0..beta_NL and tau,
@@ -111,18 +153,19 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
     r = T(1); w1 = w.g[1]; w2 = w.g[2];
   } else if constexpr (W64) {
     // mixed precision: the indicator coefficients, indicators and weights in FP64
-    const double A = (double)dx * (double)vm, Bv = (double)dx * (double)vp;
-    const double S = (double)um + (double)up, D = (double)up - (double)um, AB = A + Bv, BA = Bv - A;
+    const double Um = to_tc<double>(um), U0 = to_tc<double>(u0), Up = to_tc<double>(up), Dx = to_tc<double>(dx);
+    const double A = Dx * to_tc<double>(vm), Bv = Dx * to_tc<double>(vp);
+    const double S = Um + Up, D = Up - Um, AB = A + Bv, BA = Bv - A;
     const double e1 = 13.0 / 16.0 * D - 5.0 / 16.0 * AB;
-    const double e2 = 5.0 / 4.0 * S - 5.0 / 2.0 * (double)u0 - 3.0 / 8.0 * BA;
+    const double e2 = 5.0 / 4.0 * S - 5.0 / 2.0 * U0 - 3.0 / 8.0 * BA;
     const double e3 = 0.25 * (AB - D);
-    const double e4 = (double)u0 - 0.5 * S + 0.25 * BA;
-    const double f1 = (double)u0 - (double)um, f2 = (double)up - (double)u0;
+    const double e4 = U0 - 0.5 * S + 0.25 * BA;
+    const double f1 = U0 - Um, f2 = Up - U0;
     double beta[3] = {e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4, f1 * f1, f2 * f2};
     const double tau = 0.5 * (fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
     double r64, om[3];
     nl_weights<double, 2>(beta, tau, *w64, r64, om);
-    r = (T)r64; w1 = (T)om[1]; w2 = (T)om[2];
+    r = narrow_f64(r64); w1 = narrow_f64(om[1]); w2 = narrow_f64(om[2]);
   } else {
     // Step 2: beta = sum_l (l! c_l)^2
     T beta[3];
@@ -169,7 +212,7 @@ __device__ __forceinline__ Eig<T> eig1(T r, T m, T E, T g) {
   e.q2h = T(0.5) * e.u * e.u;
   const T p = (g - T(1)) * (E - m * e.u * T(0.5));
   const T c2 = g * p * ir;
-  e.c = sqrt(c2);
+  e.c = sqrt_t(c2);
   e.ic = rcp_t(e.c);
   e.H = (E + p) * ir;
   e.b1 = (g - T(1)) * e.ic * e.ic;
@@ -185,7 +228,7 @@ __device__ __forceinline__ Eig<T> eig2(T r, T mx, T my, T E, T g) {
   e.q2h = T(0.5) * (e.u * e.u + e.v * e.v);
   const T p = (g - T(1)) * (E - r * e.q2h);
   const T c2 = g * p * ir;
-  e.c = sqrt(c2);
+  e.c = sqrt_t(c2);
   e.ic = rcp_t(e.c);
   e.H = (E + p) * ir;
   e.b1 = (g - T(1)) * e.ic * e.ic;
@@ -294,7 +337,25 @@ __device__ __forceinline__ double euler_radius(T r, T mn, T ekin2, T E, T g) {
   // ekin2 = |m|^2 (sum of squared momenta)
   const T p = (g - T(1)) * (E - T(0.5) * ekin2 / r);
   if (!(r > T(0)) || !(p > T(0))) return __longlong_as_double(0x7ff8000000000000LL);
-  return (double)(fabs_t(mn / r) + sqrt(g * p / r));
+  return (double)(fabs_t(mn / r) + sqrt_t(g * p / r));
+}
+
+// Asynchronous 4- or 8-byte global -> shared copy (cp.async, no register
+// staging): a whole halo box can be in flight at once.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+// Waits until every cp.async this thread issued has landed.
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p));
 }
 
 // Running max of non-negative doubles through their bit patterns (exact,

@@ -68,38 +68,55 @@ struct Coef2 {
   TC dW, dE, dS, dN, q5;
 };
 
-template <typename TC, typename TQ>
+// The coefficients are evaluated on the centre-shifted averages
+// d_k = q_k - q5 (k = 1..9, k != 5): p0 reproduces constants, so c_0 gains
+// q5 and c_1..c_14 do not see it.  Every q5 term of the appendix's formulas
+// cancels exactly, and the rounding of each coefficient scales with the
+// local variation instead of with |q5| (in FP32 the difference of two nearby
+// averages is exact).  With C0 = false, c_0 is not formed (the smoothness
+// indicator does not use it).
+template <typename TC, typename TQ, bool C0 = true>
 __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
-  const TC q1 = (TC)qin[0], q2 = (TC)qin[1], q3 = (TC)qin[2], q4 = (TC)qin[3], q5 = (TC)qin[4], q6 = (TC)qin[5],
-           q7 = (TC)qin[6], q8 = (TC)qin[7], q9 = (TC)qin[8], q10 = (TC)qin[9], q11 = (TC)qin[10],
-           q12 = (TC)qin[11], q13 = (TC)qin[12], q14 = (TC)qin[13], q15 = (TC)qin[14], q16 = (TC)qin[15],
-           q17 = (TC)qin[16];
-  const TC sc = (q1 + q3) + (q7 + q9);
-  const TC cx = (q1 - q3) - (q7 - q9);
-  const TC ax = (q1 - q3) + (q7 - q9);
-  const TC ay = (q1 + q3) - (q7 + q9);
-  const TC ex = q4 + q6, ey = q2 + q8, dxe = q6 - q4, dye = q8 - q2;
+  const TC q5 = to_tc<TC>(qin[4]);
+  const TC d1 = to_tc<TC>(qin[0]) - q5, d2 = to_tc<TC>(qin[1]) - q5, d3 = to_tc<TC>(qin[2]) - q5;
+  const TC d4 = to_tc<TC>(qin[3]) - q5, d6 = to_tc<TC>(qin[5]) - q5;
+  const TC d7 = to_tc<TC>(qin[6]) - q5, d8 = to_tc<TC>(qin[7]) - q5, d9 = to_tc<TC>(qin[8]) - q5;
+  const TC q10 = to_tc<TC>(qin[9]), q11 = to_tc<TC>(qin[10]), q12 = to_tc<TC>(qin[11]);
+  const TC q13 = to_tc<TC>(qin[12]), q14 = to_tc<TC>(qin[13]), q15 = to_tc<TC>(qin[14]);
+  const TC q16 = to_tc<TC>(qin[15]), q17 = to_tc<TC>(qin[16]);
+  const TC s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
+  const TC sc = s13 + s79;        // corner sum minus 4 q5
+  const TC cx = m13 - m79;
+  const TC ax = m13 + m79;
+  const TC ay = s13 - s79;
+  const TC ex = d4 + d6, ey = d2 + d8;   // minus 2 q5 each
+  const TC dxe = d6 - d4, dye = d8 - d2;
+  const TC s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
+  const TC s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
   TC* c = o.c;
-  c[0] = (TC(5) * sc - TC(292) * (ex + ey) + TC(4028) * q5 + TC(81) * ((q11 - q10) + (q17 - q16))) *
-         TC(1.0 / 2880.0);
-  c[1] = (TC(2) * ax + TC(19) * dxe - TC(6) * (q10 + q11) + TC(3) * (q12 + q13)) * TC(1.0 / 24.0);
-  c[2] = (TC(2) * ay + TC(19) * dye + TC(3) * (q14 + q15) - TC(6) * (q16 + q17)) * TC(1.0 / 24.0);
-  c[3] = (TC(2) * ey + TC(62) * ex - sc - TC(124) * q5 + TC(18) * (q10 - q11)) * TC(1.0 / 48.0);
-  c[4] = (TC(-3) * cx - TC(5) * ((q12 - q13) + (q14 - q15))) * TC(0.125);
-  c[5] = (TC(2) * ex + TC(62) * ey - sc - TC(124) * q5 + TC(18) * (q16 - q17)) * TC(1.0 / 48.0);
-  c[6] = (TC(4) * ((q10 + q11) - dxe) - ax - TC(2) * (q12 + q13)) * TC(0.05);
-  c[7] = ((q7 + q9 - TC(2) * q8) - (q1 + q3 - TC(2) * q2)) * TC(0.25);
-  c[8] = ((q3 + q9 - TC(2) * q6) - (q1 + q7 - TC(2) * q4)) * TC(0.25);
-  c[9] = (TC(4) * ((q16 + q17) - dye) - ay - TC(2) * (q14 + q15)) * TC(0.05);
-  c[10] = (TC(4) * q5 - TC(2) * ex + (q11 - q10)) * TC(0.25);
-  c[11] = (cx + TC(2) * (q12 - q13)) * TC(0.25);
-  c[12] = (sc - TC(2) * (ex + ey) + TC(4) * q5) * TC(0.25);
-  c[13] = (cx + TC(2) * (q14 - q15)) * TC(0.25);
-  c[14] = (TC(4) * q5 - TC(2) * ey + (q17 - q16)) * TC(0.25);
-  o.dW = q5 - q4;
-  o.dE = q6 - q5;
-  o.dS = q5 - q2;
-  o.dN = q8 - q5;
+  if constexpr (C0) {
+    c[0] = q5 + (TC(5) * sc - TC(292) * (ex + ey) + TC(81) * (m1110 + m1716)) * TC(1.0 / 2880.0);
+  } else {
+    c[0] = TC(0);
+  }
+  c[1] = (TC(2) * ax + TC(19) * dxe - TC(6) * s1011 + TC(3) * s1213) * TC(1.0 / 24.0);
+  c[2] = (TC(2) * ay + TC(19) * dye + TC(3) * s1415 - TC(6) * s1617) * TC(1.0 / 24.0);
+  c[3] = (TC(2) * ey + TC(62) * ex - sc - TC(18) * m1110) * TC(1.0 / 48.0);
+  c[4] = TC(-0.375) * cx - TC(0.625) * (m1213 + m1415);
+  c[5] = (TC(2) * ex + TC(62) * ey - sc - TC(18) * m1716) * TC(1.0 / 48.0);
+  c[6] = (TC(4) * (s1011 - dxe) - ax - TC(2) * s1213) * TC(0.05);
+  c[7] = TC(-0.25) * ay - TC(0.5) * dye;
+  c[8] = TC(-0.25) * ax - TC(0.5) * dxe;
+  c[9] = (TC(4) * (s1617 - dye) - ay - TC(2) * s1415) * TC(0.05);
+  c[10] = TC(0.25) * m1110 - TC(0.5) * ex;
+  c[11] = TC(0.25) * cx + TC(0.5) * m1213;
+  c[12] = TC(0.25) * sc - TC(0.5) * (ex + ey);
+  c[13] = TC(0.25) * cx + TC(0.5) * m1415;
+  c[14] = TC(0.25) * m1716 - TC(0.5) * ey;
+  o.dW = -d4;
+  o.dE = d6;
+  o.dS = -d2;
+  o.dN = d8;
   o.q5 = q5;
 }
 
@@ -161,28 +178,27 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
 
 // Mixed precision: FP32 inputs and polynomial, but the coefficients that
 // enter the smoothness indicators, the indicators and the nonlinear weights
-// in FP64 (their epsilon-sensitive differences are where FP32 cancels).
+// in FP64 (their epsilon-sensitive differences are where FP32 cancels).  The
+// inputs are widened exactly on the integer ALU and the weights narrowed
+// (round to nearest) the same way: the hardware conversions would issue on
+// the FP64 pipe, which bounds this path.
 __device__ __forceinline__ void recon2_w64(const float* q, const WeightsT<float>& w, const WeightsT<double>& w64,
                                            bool lin, float* cu) {
+  Coef2<float> k;
+  coef2<float, float>(q, k);
   if (lin) {  // linear weights: no indicator, plain FP32 coefficients
-    Coef2<float> k;
-    coef2<float, float>(q, k);
 #pragma unroll
     for (int l = 0; l < 15; ++l) cu[l] = k.c[l];
     return;
   }
   Coef2<double> k64;
-  coef2<double, float>(q, k64);
-  Coef2<float> k;
-#pragma unroll
-  for (int l = 0; l < 15; ++l) k.c[l] = (float)k64.c[l];
-  k.dW = (float)k64.dW; k.dE = (float)k64.dE; k.dS = (float)k64.dS; k.dN = (float)k64.dN; k.q5 = q[4];
+  coef2<double, float, false>(q, k64);
   double r64, om64[5];
   weights2<double, false>(k64, w64, r64, om64, nullptr);
   float om[5];
 #pragma unroll
-  for (int m = 1; m <= 4; ++m) om[m] = (float)om64[m];
-  combine2<float>(k, (float)r64, om, w, cu);
+  for (int m = 1; m <= 4; ++m) om[m] = narrow_f64(om64[m]);
+  combine2<float>(k, narrow_f64(r64), om, w, cu);
 }
 
 // Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)

@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(256) k_features2d(const T* __restrict__ U, Gri
     };
     float centre;
     const float s = patch_scale(at, centre);
+#pragma unroll
     for (int k = 0; k < kNin; ++k) feat[c * kNin + k] = feature(at, k, centre, s);
   }
 }
@@ -327,8 +328,8 @@ __global__ void __launch_bounds__(256) k_mlp_infer2d(const T* __restrict__ U, Gr
       float centre;
       const float s = patch_scale(at, centre);
       __half* row = feat[tid];
-#pragma unroll 5
-      for (int k = 0; k < kNin; k += 2) {
+#pragma unroll
+      for (int k = 0; k < kNin; k += 2) {  // fully unrolled: patch offsets are constants
         const float lo = feature(at, k, centre, s);
         const float hi = k + 1 < kNin ? feature(at, k + 1, centre, s) : 0.0f;
         *reinterpret_cast<__half2*>(row + k) = __floats2half2_rn(lo, hi);

@@ -1,9 +1,12 @@
 // probe.cu -- measured FMA throughput of this GPU (the ALU roofline the
 // stencil kernels are compared against): a grid of 8 resident CTAs per SM,
 // each thread running 8 independent FMA chains, timed with CUDA events.
+// Also the self-check of the integer-ALU FP32 <-> FP64 conversions that the
+// mixed-precision path uses.
 #include <cuda_runtime.h>
 
 #include "hweno.h"
+#include "hweno_device.cuh"
 
 namespace {
 
@@ -48,7 +51,24 @@ double run_probe(int iters) {
   return 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
 }
 
+__global__ void k_convert_check(const float* f, double* wide, const double* d, float* narrow, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    wide[i] = hw::widen_f32(f[i]);
+    narrow[i] = hw::narrow_f64(d[i]);
+  }
+}
+
 }  // namespace
+
+extern "C" hweno_status hweno_selftest_convert(const float* f_in, double* wide_out, const double* d_in,
+                                               float* narrow_out, int n) {
+  if (n < 0 || (n > 0 && (!f_in || !wide_out || !d_in || !narrow_out))) return HWENO_ERR_ARG;
+  if (n == 0) return HWENO_OK;
+  k_convert_check<<<(n + 255) / 256, 256>>>(f_in, wide_out, d_in, narrow_out, n);
+  if (cudaGetLastError() != cudaSuccess) return HWENO_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? HWENO_OK : HWENO_ERR_CUDA;
+}
 
 extern "C" hweno_status hweno_peak_fma(int precision, double* flops_per_second) {
   if (!flops_per_second) return HWENO_ERR_ARG;

@@ -209,20 +209,40 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
     const int i0 = (tile % tiles_x) * kT2, j0 = (tile / tiles_x) * kT2;
     __syncthreads();
     const bool inner = i0 >= 2 && j0 >= 2 && i0 + kBox - 2 <= G.nx && j0 + kBox - 2 <= G.ny;
-    for (int e = threadIdx.x; e < NF * kBox * kBox; e += blockDim.x) {
-      const int f = e / (kBox * kBox), rem = e - f * (kBox * kBox);
-      const int rr = rem / kBox, cc = rem - rr * kBox;
-      int i = i0 - 2 + cc, j = j0 - 2 + rr;
-      T v;
-      if (inner) {
-        v = in[f * plane + (long long)j * G.nx + i];
-      } else {
-        i = min(max(i, -2), G.nx + 1);
-        j = min(max(j, -2), G.ny + 1);
+    if (a.stage >= 2) {
+      // The y pass's stage update reads base and hat at the tile's cells:
+      // start pulling those rows into L2 now (3 points cover every 128-byte
+      // line of a 30-cell row in either precision).
+      for (int e = threadIdx.x; e < 3 * NC * kT2 * 3; e += blockDim.x) {
+        const int pl = e / (kT2 * 3), rem = e - pl * (kT2 * 3);
+        const int rr = rem / 3, pt = rem - rr * 3;
+        const int j = min(j0 + rr, G.ny - 1), i = min(i0 + (pt == 0 ? 0 : (pt == 1 ? 15 : kT2 - 1)), G.nx - 1);
+        const T* src = pl < NC ? base + pl * plane : hat + (pl - NC) * plane;
+        prefetch_l2(src + (long long)j * G.nx + i);
+      }
+    }
+    if (inner) {
+      // whole box in flight at once; ghost-free, so a plain copy: a warp per
+      // box row (34 cells: lanes 0-31, then lanes 0-1 for the last two)
+      const T* src0 = in + (long long)(j0 - 2) * G.nx + (i0 - 2);
+      for (int row = warp; row < NF * kBox; row += nwarps) {
+        const int f = row / kBox, rr = row - f * kBox;
+        const T* srow = src0 + f * plane + (long long)rr * G.nx;
+        T* drow = box + f * kFS + rr * kBP;
+        cp_async_elem(drow + lane, srow + lane);
+        if (lane < kBox - 32) cp_async_elem(drow + 32 + lane, srow + 32 + lane);
+      }
+      cp_async_wait_all();
+    } else {
+      for (int e = threadIdx.x; e < NF * kBox * kBox; e += blockDim.x) {
+        const int f = e / (kBox * kBox), rem = e - f * (kBox * kBox);
+        const int rr = rem / kBox, cc = rem - rr * kBox;
+        const int i = min(max(i0 - 2 + cc, -2), G.nx + 1), j = min(max(j0 - 2 + rr, -2), G.ny + 1);
+        T v;
         if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
         else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j);
+        box[f * kFS + rr * kBP + cc] = v;
       }
-      box[f * kFS + rr * kBP + cc] = v;
     }
     __syncthreads();
 

@@ -30,6 +30,7 @@ EXPORTS = (
     "hweno_last_error", "hweno_version", "hweno_create", "hweno_destroy", "hweno_stream",
     "hweno_shape", "hweno_set_state", "hweno_get_state", "hweno_alpha", "hweno_apply_operator",
     "hweno_step", "hweno_advance", "hweno_set_profiling", "hweno_profile", "hweno_peak_fma",
+    "hweno_selftest_convert",
     "hweno_batch_create", "hweno_batch_destroy",
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
     "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
@@ -143,6 +144,7 @@ def load():
     L.hweno_set_profiling.argtypes = [vp, C.c_int]
     L.hweno_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     L.hweno_peak_fma.argtypes = [C.c_int, C.POINTER(C.c_double)]
+    L.hweno_selftest_convert.argtypes = [vp, vp, vp, vp, C.c_int]
     L.hweno_batch_create.argtypes = [C.c_int, cp, vp, C.POINTER(vp)]
     L.hweno_batch_destroy.argtypes = [vp]
     L.hweno_batch_destroy.restype = None
@@ -269,6 +271,21 @@ def hweno_peak_fma(precision: int) -> float:
     f = C.c_double()
     _check(load().hweno_peak_fma(precision, C.byref(f)))
     return f.value
+
+
+def hweno_selftest_convert(f_in, d_in):
+    """f_in: float32 device tensor, d_in: float64 device tensor of the same
+    length; returns (f_in widened to float64, d_in rounded to float32) as the
+    library's integer-ALU conversions compute them."""
+    import torch
+    n = f_in.numel()
+    if d_in.numel() != n or f_in.dtype != torch.float32 or d_in.dtype != torch.float64:
+        raise ValueError("f_in float32 and d_in float64 of equal length")
+    f_in, d_in = f_in.contiguous(), d_in.contiguous()
+    wide = torch.empty(n, dtype=torch.float64, device=f_in.device)
+    narrow = torch.empty(n, dtype=torch.float32, device=f_in.device)
+    _check(load().hweno_selftest_convert(f_in.data_ptr(), wide.data_ptr(), d_in.data_ptr(), narrow.data_ptr(), n))
+    return wide, narrow
 
 
 def hweno_batch_create(cfgs, stream=None):

@@ -408,3 +408,94 @@ def test_checkpoint_resume_is_bitwise(tmp_path):
     tc, _ = hw.hweno_get_time(c.h)
     assert ta == tc
     assert np.array_equal(a.get_state(device=False), c.get_state(device=False))
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_constant_state_is_steady(dim):
+    """Degenerate case: a constant state (zero normal velocity at reflective
+    walls, the same state at inflow sides) has L = 0 up to round-off under
+    every boundary condition, and limited derivatives 0."""
+    if dim == 1:
+        st = W.prim_to_cons_1d(1.3, 0.0, 0.7)
+        n = 61
+        U = np.concatenate([np.repeat(st[:, None], n, axis=1), np.zeros((3, n))])
+        bcs = [(0, 0), (1, 1), (2, 2), (3, 3)]
+    else:
+        st = W.prim_to_cons_2d(1.3, 0.0, 0.0, 0.7)
+        n = 37
+        U = np.concatenate([np.repeat(np.repeat(st[:, None, None], n, 1), n, 2), np.zeros((8, n, n))])
+        bcs = [(0, 0, 0, 0), (1, 1, 1, 1), (2, 2, 2, 2), (3, 3, 3, 3), (2, 1, 0, 0)]
+    for bc in bcs:
+        stt = [list(st) + [0.0] * (4 - len(st))] * 4
+        prob = oracle.Problem(dim=dim, equation=oracle.EQ_EULER, nx=n, ny=n, lin_w=W2D if dim == 2 else (0.995, 0.0025, 0.0025),
+                              bc=tuple(bc) + (0,) * (4 - len(bc)), bc_state=stt)
+        s = hw.Solver(cfg_from(prob))
+        s.set_state(U)
+        L, D = s.apply_operator(2.0, 2.0)
+        L = L.cpu().numpy()
+        scale = 2.0 * np.abs(st).max() / prob.dx
+        assert np.abs(L).max() < 1e-13 * scale, (bc, np.abs(L).max())
+        assert np.abs(D.cpu().numpy()).max() < 1e-13 * np.abs(st).max()
+        s.close()
+
+
+def _window_operator(prob, U, i, j, ax, ay, r=3, rel=0.0, samples=4):
+    """Oracle L and D at cell (i, j) from a (2r+1)^2 window around it (the
+    operator at a cell depends on a radius-2 neighbourhood only), and their
+    absolute spread under random relative input perturbations of size `rel`
+    (the condition of that cell's outputs at the working precision)."""
+    sub = np.ascontiguousarray(U[:, j - r:j + r + 1, i - r:i + r + 1])
+    m = 2 * r + 1
+    p = oracle.Problem(dim=2, equation=prob.equation, nx=m, ny=m, xlo=0, xhi=m * prob.dx, ylo=0,
+                       yhi=m * prob.dy, lin_w=prob.lin_w, bc=(1, 1, 1, 1))
+    L, D = oracle.operator(p, sub, ax, ay)
+    L0, D0 = L[:, r, r], D[:, r, r]
+    sL, sD = np.zeros_like(L0), np.zeros_like(D0)
+    rng = np.random.default_rng(i * 7919 + j)
+    for _ in range(samples if rel > 0 else 0):
+        sp = sub * (1.0 + rel * rng.choice([-1.0, 1.0], size=sub.shape) * rng.uniform(0.5, 1.0, size=sub.shape))
+        L1, D1 = oracle.operator(p, sp, ax, ay)
+        sL = np.maximum(sL, np.abs(L1[:, r, r] - L0))
+        sD = np.maximum(sD, np.abs(D1[:, r, r] - D0))
+    return L0, D0, sL, sD
+
+
+@pytest.mark.parametrize("precision", [hw.FP64, hw.FP32_IND64])
+def test_full_size_sampled_parity(precision):
+    """The bench's 4096^2 four-quadrant state, launch shape autotuned as in
+    bench.py: one operator application, 60 sampled cells (a third on the
+    discontinuities) against oracle windows.  Per output: within 1e-12 (FP64)
+    or 2e-5 (mixed precision: FP32 storage and stencil) of the plane's scale,
+    or within 100x the oracle's own spread at that cell under unit-roundoff
+    input perturbations."""
+    n = 4096
+    U = W.quadrant_2d(W.quadrant_states(2024), 0.5, 0.5, 0.0, 1.0, 0.0, 1.0, n, n)
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=n, ny=n, lin_w=W2D, bc=(1, 1, 1, 1))
+    s = hw.Solver(cfg_from(prob, precision))
+    s.set_state(torch.from_numpy(U).cuda())
+    hw.hweno_autotune(s.h, reps=1)
+    ax, ay = 2.5, 2.3
+    L, D = s.apply_operator(ax, ay)
+    Lh = L.double().cpu().numpy()
+    Dh = D.double().cpu().numpy()
+    del L, D
+    s.close()
+    Uin = U if precision == hw.FP64 else U.astype(np.float32).astype(np.float64)
+    rel = 2.0 ** -53 if precision == hw.FP64 else 2.0 ** -24
+    rng = np.random.default_rng(17)
+    cells = [(int(a), int(b)) for a, b in rng.integers(8, n - 8, size=(40, 2))]
+    cells += [(2048 + int(d), int(b)) for d, b in zip(rng.integers(-3, 3, 10), rng.integers(8, n - 8, 10))]
+    cells += [(int(b), 2048 + int(d)) for d, b in zip(rng.integers(-3, 3, 10), rng.integers(8, n - 8, 10))]
+    Lmax = np.abs(Lh).reshape(Lh.shape[0], -1).max(axis=1)
+    # The limited derivatives are scaled moments (units of the averages): on
+    # this piecewise-constant state they are rounding noise of size ~1e-7, so
+    # their scale is the larger of their own plane maximum and that of the
+    # matching average plane.
+    nc = U.shape[0] // 3
+    Umax = np.abs(U[:nc]).reshape(nc, -1).max(axis=1)
+    Dmax = np.maximum(np.abs(Dh).reshape(Dh.shape[0], -1).max(axis=1), np.concatenate([Umax, Umax]))
+    tol = 1e-12 if precision == hw.FP64 else 2e-5
+    for (i, j) in cells:
+        Lr, Dr, sL, sD = _window_operator(prob, Uin, i, j, ax, ay, rel=rel)
+        assert np.all(np.abs(Lh[:, j, i] - Lr) <= np.maximum(tol * Lmax, 100.0 * sL)), (i, j)
+        assert np.all(np.abs(Dh[:, j, i] - Dr) <= np.maximum(tol * Dmax, 100.0 * sD)), (i, j)
