@@ -37,6 +37,15 @@ W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
 # Algorithmic flops of one cell update in one stage, counted from the
 # executed FP instructions of the stage kernel (ncu sass op counters, see
 # profiles/) with the ring-cell redundancy of the two passes removed.
+# bench arms: (name, precision, learned indicator, scheme options).  FP64
+# plain (the reference), FP32, FP32 with FP64 smoothness indicators (the
+# headline), both FP32 forms with the learned troubled-cell indicator, and
+# two variants of the headline: the Jiang-Shu indicator the paper replaces
+# and the component-wise (non-characteristic) Euler reconstruction.
+ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64", "FP32_IND64", False, {}),
+        ("fp32_learned", "FP32", True, {}), ("fp32_ind64_learned", "FP32_IND64", True, {}),
+        ("fp32_ind64_typical", "FP32_IND64", False, {"smoothness": "BETA_TYPICAL"}),
+        ("fp32_ind64_component", "FP32_IND64", False, {"charwise": 0})]
 FLOPS_PER_CELL_STAGE = {"fp64": 5842.0, "fp32": 5466.0, "fp32_ind64": 1889.0}
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
                 "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); the "
@@ -198,12 +207,13 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def time_arm(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, theta=None):
+def time_arm(hw, torch, U0_dev, precision, steps, warmup, sampler_gpu, theta=None, extra=None):
     """Advance `steps` steps of the workload at `precision` (optionally with
-    the learned indicator); returns timings and the final density."""
+    the learned indicator, and with scheme options `extra`); returns timings
+    and the final density."""
     n = GRID["n"]
     cfg = hw.Config(dim=2, nx=n, ny=n, equation=hw.EQ_EULER, lin_w=W2D, bc=(hw.BC_OUTFLOW,) * 4,
-                    precision=precision)
+                    precision=precision, **(extra or {}))
     s = hw.Solver(cfg)
     if theta is not None:
         hw.hweno_indicator_load(s.h, theta, 0.5)
@@ -343,8 +353,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=N_GRID, help="cells per side (profiling runs use a small grid)")
-    ap.add_argument("--only", choices=["fp64", "fp32", "fp32_ind64", "fp32_learned", "fp32_ind64_learned"],
-                    default=None, help="time one arm only (profiling runs)")
+    ap.add_argument("--only", choices=[a[0] for a in ARMS], default=None,
+                    help="time one arm only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["euler2d_quadrant", "batch1d"], default="euler2d_quadrant",
                     help="batch1d: 256 seeded 1D Euler Riemann problems of uneven sizes in one batch")
@@ -374,21 +384,19 @@ def main():
     U0_pin = U0_t.pin_memory()
     U0_dev = U0_pin.cuda()
 
-    # arms: FP64 plain (the reference), FP32, FP32 with FP64 smoothness
-    # indicators and weights (the headline), and both FP32 forms with the
-    # learned troubled-cell indicator
-    plan = [("fp64", hw.FP64, False), ("fp32", hw.FP32, False), ("fp32_ind64", hw.FP32_IND64, False),
-            ("fp32_learned", hw.FP32, True), ("fp32_ind64_learned", hw.FP32_IND64, True)]
+    plan = [(name, getattr(hw, prec), learned, extra) for name, prec, learned, extra in ARMS]
     if args.only is not None:
         plan = [p for p in plan if p[0] == args.only]
     theta = ind_eval = None
-    if any(learned for _, _, learned in plan):
+    if any(p[2] for p in plan):
         theta, ind_eval, _ = train_indicator()
     arms = {}
-    for name, prec, learned in plan:
+    for name, prec, learned, extra in plan:
+        opts = {k: getattr(hw, v) if isinstance(v, str) else v for k, v in extra.items()}
         arms[name] = time_arm(hw, torch, U0_dev, prec, args.steps, args.warmup, local,
-                              theta=theta if learned else None)
+                              theta=theta if learned else None, extra=opts)
         arms[name]["precision"] = prec
+        arms[name]["variant"] = extra
     head_name = "fp32_ind64" if "fp32_ind64" in arms else next(iter(arms))
     head = arms[head_name]
     ms_head = head["ms"]
@@ -418,10 +426,10 @@ def main():
 
     def roofline(r, prec, peak_tf, learned=False):
         key = "fp64" if prec == hw.FP64 else ("fp32_ind64" if prec == hw.FP32_IND64 else "fp32")
-        if learned:
-            key = key + "_learned"
-        fl = FLOPS_PER_CELL_STAGE.get(key)
-        traffic = TRAFFIC_PER_CELL.get(key)
+        if learned or r["variant"]:
+            key = None   # other kernel paths: not counted
+        fl = FLOPS_PER_CELL_STAGE.get(key) if key else None
+        traffic = TRAFFIC_PER_CELL.get(key) if key else None
         out = {"bound": "alu", "peak": peak_tf, "unit": "TFLOP/s",
                "kernel": f"k_stage2d<{'double' if prec == hw.FP64 else 'float'},EULER,char"
                          f"{',fp64 weights' if prec == hw.FP32_IND64 else ''}>",
@@ -459,6 +467,8 @@ def main():
                 out["speedup_vs_fp64"] = arms["fp64"]["ms"] / r["ms"]
         if r["smooth_fraction"] is not None:
             out["linear_path_fraction"] = r["smooth_fraction"]
+        if r["variant"]:
+            out["variant"] = r["variant"]
         return out
 
     cpu = None

@@ -60,6 +60,7 @@ enum { HWENO_EQ_ADVECTION = 0, HWENO_EQ_BURGERS = 1, HWENO_EQ_EULER = 2 };
 enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECT = 2, HWENO_BC_INFLOW = 3 };
 enum { HWENO_FP64 = 0, HWENO_FP32 = 1, HWENO_FP32_IND64 = 2 };
 enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
+enum { HWENO_BETA_MOMENT = 0, HWENO_BETA_TYPICAL = 1 };
 
 /* Problem statement and scheme parameters.
  *  dim            1 or 2
@@ -84,7 +85,14 @@ enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
  *  precision      HWENO_FP64, HWENO_FP32 (storage and stencil arithmetic), or
  *                 HWENO_FP32_IND64 (FP32 storage and stencil arithmetic; the
  *                 coefficients entering the smoothness indicators, the
- *                 indicators and the nonlinear weights in FP64)
+ *                 indicators, tau and tau^2/(beta + eps) in FP64, the
+ *                 normalisation of the nonlinear weights in FP32)
+ *  smoothness     HWENO_BETA_MOMENT: the paper's indicator (Step 2 of Sec. 2.1
+ *                 and 2.2, sum of squared scaled derivatives at the cell
+ *                 centre); HWENO_BETA_TYPICAL: the Jiang-Shu integral
+ *                 indicator it replaces, Eq. (smoothness-indicator-typical)
+ *                 and its 2D form (cell means of the squared scaled
+ *                 derivatives; identical for the linear polynomials)
  */
 typedef struct {
   int dim;
@@ -102,6 +110,7 @@ typedef struct {
   int bc[4];
   double bc_state[4][4];
   int precision;
+  int smoothness;
 } hweno_config;
 
 typedef struct hweno_solver hweno_solver;

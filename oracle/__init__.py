@@ -26,6 +26,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
 DT_CFL, DT_CFL_DX53 = 0, 1
+BETA_MOMENT, BETA_TYPICAL = 0, 1
 
 
 def build(force: bool = False) -> str:
@@ -49,7 +50,7 @@ class _Problem(C.Structure):
         ("lin_w", C.c_double * 5), ("eps", C.c_double),
         ("weight_pow", C.c_int), ("charwise", C.c_int), ("linear_weights", C.c_int),
         ("dt_rule", C.c_int), ("bc", C.c_int * 4), ("bc_state", (C.c_double * 4) * 4),
-        ("cfl", C.c_double),
+        ("cfl", C.c_double), ("smoothness", C.c_int),
     ]
 
 
@@ -76,6 +77,7 @@ class Problem:
     bc: tuple = (BC_PERIODIC,) * 4
     bc_state: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])
     cfl: float = 0.6
+    smoothness: int = BETA_MOMENT  # BETA_TYPICAL: the Jiang-Shu integral indicator
 
     @property
     def ncomp(self) -> int:
@@ -117,6 +119,7 @@ class Problem:
             for c in range(4):
                 s.bc_state[k][c] = self.bc_state[k][c]
         s.cfl = self.cfl
+        s.smoothness = self.smoothness
         return s
 
 

@@ -196,6 +196,40 @@ void or_coef_maps_2d(double* G0, double* Gm) {
 /* ------------------------------------------------------------------------ */
 /* Steps 2-3: smoothness indicators and nonlinear weights.                  */
 /* ------------------------------------------------------------------------ */
+/* Jiang-Shu indicator, Eq. (smoothness-indicator-typical) and its 2D form:
+ * beta = sum over derivative orders 1 <= l <= deg of the cell mean of
+ * (dx^m dy^n d^(m+n) p / dx^m dy^n)^2 over m + n = l; in the cell's scaled
+ * coordinates (xi, eta) in [-1/2, 1/2]^2 this is the plain integral of the
+ * squared xi/eta derivatives.  Evaluated by 4-point Gauss-Legendre rules
+ * (exact up to degree 7 per variable; the squared derivatives of a quartic
+ * have degree <= 6). */
+static const double GL4_X[4] = {-0.43056815579702629, -0.16999052179242813, 0.16999052179242813,
+                                0.43056815579702629};  /* on [-1/2, 1/2] */
+static const double GL4_W[4] = {0.17392742256872693, 0.32607257743127307, 0.32607257743127307,
+                                0.17392742256872693};  /* sum 1 */
+
+
+/* d^l/dxi^l of p(xi) = sum_k c[k] xi^k, k < nc */
+static double poly1_deriv(const double* c, int nc, double xi, int l) {
+  double s = 0.0;
+  for (int k = l; k < nc; ++k) {
+    double f = 1.0;
+    for (int j = 0; j < l; ++j) f *= (k - j);
+    s += c[k] * f * pw(xi, k - l);
+  }
+  return s;
+}
+
+static double beta_typical_1d(const double* c, int nc) {
+  double b = 0.0;
+  for (int l = 1; l < nc; ++l)
+    for (int g = 0; g < 4; ++g) {
+      const double d = poly1_deriv(c, nc, GL4_X[g], l);
+      b += GL4_W[g] * d * d;
+    }
+  return b;
+}
+
 /* tau = (sum_m |beta_0 - beta_m|) / nlin  (Sec. 2.1: /2, Sec. 2.2: /4);
  * w~_m = gamma_m (1 + tau^2 / (beta_m^pow + eps)); w = w~ / sum w~.        */
 static void nonlinear_weights(const or_problem* p, int nlin, const double* beta, double* w) {
@@ -236,6 +270,11 @@ int or_recon_cell_1d(const or_problem* p, const double* in, double dx, double* o
   /* Step 2: beta = sum_{l>=1} (l! c_l)^2 */
   double beta[3] = {0.0, c1[1] * c1[1], c2[1] * c2[1]};
   for (int l = 1; l < 5; ++l) beta[0] += (FACT[l] * c0[l]) * (FACT[l] * c0[l]);
+  if (p->smoothness == OR_BETA_TYPICAL) {
+    beta[0] = beta_typical_1d(c0, 5);
+    beta[1] = beta_typical_1d(c1, 2);
+    beta[2] = beta_typical_1d(c2, 2);
+  }
   /* Step 3: weights and Eq. (hweno-reconstruction-1D) */
   double w[3];
   nonlinear_weights(p, 2, beta, w);
@@ -284,6 +323,18 @@ static double poly2_eval(const double* c, double xi, double eta, int dxi, int de
   return s;
 }
 
+static double beta_typical_2d(const double* c) {
+  double b = 0.0;
+  for (int l = 1; l <= 4; ++l)
+    for (int m = 0; m <= l; ++m)
+      for (int gx = 0; gx < 4; ++gx)
+        for (int gy = 0; gy < 4; ++gy) {
+          const double d = poly2_eval(c, GL4_X[gx], GL4_X[gy], m, l - m);
+          b += GL4_W[gx] * GL4_W[gy] * d * d;
+        }
+  return b;
+}
+
 int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy, double* out) {
   build_maps();
   /* Step 1 */
@@ -308,6 +359,13 @@ int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy,
     beta[0] += f * f;
   }
   for (int m = 0; m < 4; ++m) beta[m + 1] = cm[m][1] * cm[m][1] + cm[m][2] * cm[m][2];
+  if (p->smoothness == OR_BETA_TYPICAL) {
+    beta[0] = beta_typical_2d(c0);
+    for (int m = 0; m < 4; ++m) {
+      const double lin[15] = {cm[m][0], cm[m][1], cm[m][2]};
+      beta[m + 1] = beta_typical_2d(lin);
+    }
+  }
   /* Step 3: weights and Eq. (hweno-reconstruction-2D) */
   double w[5];
   nonlinear_weights(p, 4, beta, w);

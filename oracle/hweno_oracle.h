@@ -46,7 +46,11 @@ typedef struct {
   int bc[4];                /* x-low, x-high, y-low, y-high: OR_BC_* */
   double bc_state[4][4];    /* conservative state used by OR_BC_INFLOW sides */
   double cfl;
+  int smoothness;           /* OR_BETA_MOMENT: Step 2's indicator (the paper's);
+                               OR_BETA_TYPICAL: the Jiang-Shu integral indicator that
+                               Step 2 replaces, Eq. (smoothness-indicator-typical[-2D]) */
 } or_problem;
+enum { OR_BETA_MOMENT = 0, OR_BETA_TYPICAL = 1 };
 
 /* Number of components (1, 3 or 4) and of stored fields per cell. */
 int or_ncomp(const or_problem* p);

@@ -70,6 +70,8 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
   if (std::fabs(s - 1.0) > 1e-12) return fail(HWENO_ERR_ARG, "linear weights must sum to 1 (sum %.17g)", s);
   if (!(c->eps > 0.0)) return fail(HWENO_ERR_ARG, "eps must be positive");
   if (c->weight_pow != 1 && c->weight_pow != 2) return fail(HWENO_ERR_ARG, "weight_pow must be 1 or 2");
+  if (c->smoothness != HWENO_BETA_MOMENT && c->smoothness != HWENO_BETA_TYPICAL)
+    return fail(HWENO_ERR_ARG, "smoothness must be HWENO_BETA_MOMENT or HWENO_BETA_TYPICAL");
   if (!(c->cfl > 0.0)) return fail(HWENO_ERR_ARG, "cfl must be positive");
   if (c->dt_rule != HWENO_DT_CFL && c->dt_rule != HWENO_DT_CFL_DX53) return fail(HWENO_ERR_ARG, "bad dt_rule");
   if (c->precision != HWENO_FP64 && c->precision != HWENO_FP32 && c->precision != HWENO_FP32_IND64)
@@ -158,10 +160,7 @@ struct Engine {
     HW_CK(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
     HW_CK(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
     HW_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    for (int m = 0; m < 5; ++m) wp.g[m] = cfg.lin_w[m];
-    wp.eps = cfg.eps;
-    wp.pow2 = cfg.weight_pow == 2;
-    wp.linear = cfg.linear_weights != 0;
+    wp = hw::weight_params(cfg);
 
     ctl_init.resize(n);
     if (dim == 1) {
@@ -255,6 +254,7 @@ struct Engine {
       a.in = in; a.base = S; a.out = out; a.hat = hat;
       a.grid = grid; a.ctl = c; a.ax_op = ax; a.ay_op = ay; a.stage = s;
       a.gamma_gas = cfg.gamma_gas; a.adv_x = cfg.adv_x; a.adv_y = cfg.adv_y; a.wp = wp;
+      a.f32 = hw::stage2_f32(grid, ax, ay, cfg.gamma_gas, cfg.adv_x, cfg.adv_y);
       a.plane = cells;
       a.smooth = learned && s > 0 ? smooth : nullptr;
       HW_CK(hw::launch_stage2d(prec, cfg.equation, cfg.charwise, a, num_sms, own, shape));
@@ -433,6 +433,9 @@ struct Engine {
       ctl_host[k].dt = dt;
       ctl_host[k].ax = ax;
       ctl_host[k].ay = ay;
+      ctl_host[k].dtf = (float)dt;
+      ctl_host[k].axf = (float)ax;
+      ctl_host[k].ayf = (float)ay;
       ctl_host[k].done = 0;
     }
     HW_CK(cudaMemcpyAsync(ctl_manual, ctl_host, sizeof(hw::Ctl) * n_inst, cudaMemcpyHostToDevice, own));
@@ -683,6 +686,7 @@ hweno_status hweno_batch_create(int n, const hweno_config* cfgs, void* cuda_stre
     const hweno_config &a = cfgs[0], &b = cfgs[k];
     bool same = a.equation == b.equation && a.precision == b.precision && a.charwise == b.charwise &&
                 a.linear_weights == b.linear_weights && a.weight_pow == b.weight_pow && a.eps == b.eps &&
+                a.smoothness == b.smoothness &&
                 a.gamma_gas == b.gamma_gas && a.adv_x == b.adv_x;
     for (int m = 0; m < 3; ++m) same = same && a.lin_w[m] == b.lin_w[m];
     if (!same) return fail(HWENO_ERR_ARG, "config %d differs from config 0 in a batch-wide parameter", k);

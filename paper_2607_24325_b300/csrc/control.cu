@@ -37,6 +37,9 @@ __global__ void k_ctl_begin(Ctl* ctl, int n, int dim) {
     c->last = 1;
   }
   c->dt = dt;
+  c->dtf = (float)dt;
+  c->axf = (float)c->ax;
+  c->ayf = (float)c->ay;
 }
 
 __global__ void k_ctl_end(Ctl* ctl, int n) {

@@ -24,17 +24,36 @@ struct WeightsT {
   T eps;         // epsilon of the nonlinear weights
   int pow2;      // 1: beta^2 + eps in the denominator, 0: beta + eps
   int linear;    // 1: omega = gamma (pure p0)
+  int typical;   // 1: Jiang-Shu integral indicator for p0
 };
 
 template <typename T>
 __host__ __device__ inline WeightsT<T> make_weights(const WeightParams& w) {
   WeightsT<T> o;
-  for (int m = 0; m < 5; ++m) o.g[m] = (T)w.g[m];
-  o.inv_g0 = (T)(1.0 / w.g[0]);
-  o.eps = (T)w.eps;
+  if constexpr (sizeof(T) == 4) {
+    for (int m = 0; m < 5; ++m) o.g[m] = w.gf[m];
+    o.inv_g0 = w.inv_g0f;
+    o.eps = w.epsf;
+  } else {
+    for (int m = 0; m < 5; ++m) o.g[m] = (T)w.g[m];
+    o.inv_g0 = (T)(1.0 / w.g[0]);
+    o.eps = (T)w.eps;
+  }
   o.pow2 = w.pow2;
   o.linear = w.linear;
+  o.typical = w.typical;
   return o;
+}
+
+// Jiang-Shu indicator of a quartic in the cell's scaled coordinate,
+// Eq. (smoothness-indicator-typical): sum_{l=1..4} int_{-1/2}^{1/2}
+// (d^l p / dxi^l)^2 dxi as the closed quadratic form in c_1..c_4 (the odd
+// monomial moments vanish).  For a linear polynomial it is c_1^2, the same
+// as the moment form.
+template <typename T>
+__device__ __forceinline__ T beta_typical_1d(T c1, T c2, T c3, T c4) {
+  return c1 * (c1 + T(0.5) * c3) + c2 * (T(13.0 / 3.0) * c2 + T(4.2) * c4) + T(3129.0 / 80.0) * c3 * c3 +
+         T(87617.0 / 140.0) * c4 * c4;
 }
 
 template <typename T>
@@ -42,10 +61,17 @@ __device__ __forceinline__ T fabs_t(T x) { return x < T(0) ? -x : x; }
 
 // Reciprocal and quotient: IEEE in FP64; in FP32 the fast approximate forms
 // (a few ulp), far below the FP32 stencil's own conditioning.
+// FP32: the hardware approximate reciprocal (PTX rcp.approx.ftz.f32, about
+// 1 ulp) and a quotient as a times that reciprocal.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float rcp_t(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double div_t(double a, double b) { return a / b; }
-__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float div_t(float a, float b) { return a * rcp_approx(b); }
 // Square root in the argument's own precision (an unqualified sqrt of a
 // float would promote to the FP64 pipe).
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
@@ -80,6 +106,30 @@ __device__ __forceinline__ float narrow_f64(double x) {
   unsigned bits = (hi & 0x80000000u) | ((e - 896u) << 23) | frac;
   bits += (rest > 0x10000000u || (rest == 0x10000000u && (frac & 1u))) ? 1u : 0u;
   return __uint_as_float(bits);
+}
+
+// As narrow_f64, but magnitudes below the smallest normal FP32 number
+// become zero (no FP64-pipe fallback for them).
+__device__ __forceinline__ float narrow_f64_ftz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  if (((hi >> 20) & 0x7ffu) < 897u) return __uint_as_float(hi & 0x80000000u);
+  return narrow_f64(x);
+}
+
+// 1/s for a positive normal double: an FP32 seed (the approximate reciprocal
+// of s's significand, exponent handled on the integer ALU) and one Newton
+// step y <- y + y (1 - s y) in FP64, relative error about 2^-46 -- two FP64
+// operations instead of an IEEE division.  Exponents near the ends of the
+// range take the division.
+__device__ __forceinline__ double rcp_newton(double s) {
+  const unsigned hi = (unsigned)__double2hiint(s), lo = (unsigned)__double2loint(s);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e < 2 || e > 2044) return 1.0 / s;
+  const float m = __uint_as_float(0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));  // in [1, 2)
+  const double y0 = widen_f32(rcp_approx(m));                                         // in (0.5, 1]
+  const unsigned yh = (unsigned)__double2hiint(y0) - ((unsigned)(e - 1023) << 20);
+  const double y = __hiloint2double((int)yh, __double2loint(y0));
+  return fma(y, fma(-s, y, 1.0), y);
 }
 
 // Input conversion of the coefficient maps: identity, or the exact widening.
@@ -161,7 +211,9 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
     const double e3 = 0.25 * (AB - D);
     const double e4 = U0 - 0.5 * S + 0.25 * BA;
     const double f1 = U0 - Um, f2 = Up - U0;
-    double beta[3] = {e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4, f1 * f1, f2 * f2};
+    double beta[3] = {w.typical ? beta_typical_1d(e1, e2, e3, e4)
+                                : e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4,
+                      f1 * f1, f2 * f2};
     const double tau = 0.5 * (fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
     double r64, om[3];
     nl_weights<double, 2>(beta, tau, *w64, r64, om);
@@ -169,7 +221,8 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
   } else {
     // Step 2: beta = sum_l (l! c_l)^2
     T beta[3];
-    beta[0] = c1 * c1 + T(4) * c2 * c2 + T(36) * c3 * c3 + T(576) * c4 * c4;
+    beta[0] = w.typical ? beta_typical_1d(c1, c2, c3, c4)
+                        : c1 * c1 + T(4) * c2 * c2 + T(36) * c3 * c3 + T(576) * c4 * c4;
     beta[1] = d1 * d1;
     beta[2] = d2 * d2;
     // Step 3

@@ -14,7 +14,18 @@ constexpr int kBox = 34;          // tile + 2 halo cells per side
 constexpr int kBP = 35;           // box pitch (odd: conflict-free column walks)
 constexpr int kFS = kBox * kBP;   // box field stride
 constexpr int kSP = 30;           // stash pitch
-constexpr int kSS = kT2 * kSP;    // stash field stride
+constexpr int kSS = kT2 * kSP + 4;  // stash field stride (room for the row skew)
+
+// Stash offset of tile cell (row r, column c).  The x pass writes rows
+// (consecutive lanes, consecutive words); the y pass reads columns (lane =
+// row, stride kSP).  A stride of 30 words alone would pair lanes l and l+16
+// (FP32) or l and l+8 (FP64, two banks per element) on one bank; skewing
+// every 16th (FP32) or 8th (FP64) row by one element keeps both walks
+// conflict-free.
+template <typename T>
+__device__ __forceinline__ int stash_at(int r, int c) {
+  return r * kSP + c + (r >> (sizeof(T) == 8 ? 3 : 4));
+}
 constexpr int kThreads2 = 256;
 
 template <int NC>
@@ -120,6 +131,28 @@ __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
   o.q5 = q5;
 }
 
+// Jiang-Shu indicator of the 2D quartic, the 2D form of Eq.
+// (smoothness-indicator-typical): the sum over 1 <= m + n <= 4 of the
+// integrals over [-1/2, 1/2]^2 of (d^{m+n} p / dxi^m deta^n)^2, as the
+// closed quadratic form in c_1..c_14 (29 terms; the odd monomial moments
+// vanish), grouped by the first coefficient of each product.
+template <typename T>
+__device__ __forceinline__ T beta_typical_2d(const T* c) {
+  T b = c[1] * (c[1] + T(0.5) * c[6] + T(1.0 / 6.0) * c[8]);
+  b += c[2] * (c[2] + T(1.0 / 6.0) * c[7] + T(0.5) * c[9]);
+  b += c[3] * (T(13.0 / 3.0) * c[3] + T(4.2) * c[10] + T(13.0 / 18.0) * c[12]);
+  b += c[5] * (T(13.0 / 3.0) * c[5] + T(4.2) * c[14] + T(13.0 / 18.0) * c[12]);
+  b += c[4] * (T(7.0 / 6.0) * c[4] + T(17.0 / 30.0) * (c[11] + c[13]));
+  b += c[6] * (T(3129.0 / 80.0) * c[6] + T(1.0 / 24.0) * c[8]);
+  b += c[9] * (T(3129.0 / 80.0) * c[9] + T(1.0 / 24.0) * c[7]);
+  b += T(3389.0 / 720.0) * (c[7] * c[7] + c[8] * c[8]);
+  b += c[10] * (T(87617.0 / 140.0) * c[10] + T(0.35) * c[12]);
+  b += c[14] * (T(87617.0 / 140.0) * c[14] + T(0.35) * c[12]);
+  b += c[11] * (T(47459.0 / 1120.0) * c[11] + T(11.0 / 80.0) * c[13]);
+  b += T(47459.0 / 1120.0) * c[13] * c[13] + T(6799.0 / 360.0) * c[12] * c[12];
+  return b;
+}
+
 // Steps 2-3 (Sec. 2.2): beta = sum (m! n! c)^2, tau = 1/4 sum |beta_0 - beta_m|,
 // the nonlinear weights; r = omega_0 / gamma_0 and om[1..4].  With DEV the
 // largest |omega_m / gamma_m - 1| is folded into *dev.
@@ -128,10 +161,11 @@ __device__ __forceinline__ void weights2(const Coef2<TW>& k, const WeightsT<TW>&
   const TW* c = k.c;
   const TW b1 = k.dW * k.dW + k.dS * k.dS, b2 = k.dE * k.dE + k.dS * k.dS;
   const TW b3 = k.dE * k.dE + k.dN * k.dN, b4 = k.dW * k.dW + k.dN * k.dN;
-  const TW b0 = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
-                TW(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
-                TW(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
-                TW(576) * (c[10] * c[10] + c[14] * c[14]) + TW(16) * c[12] * c[12];
+  const TW b0 = w.typical ? beta_typical_2d(c)
+                          : c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
+                                TW(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
+                                TW(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
+                                TW(576) * (c[10] * c[10] + c[14] * c[14]) + TW(16) * c[12] * c[12];
   const TW tau = TW(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
   const TW beta[5] = {b0, b1, b2, b3, b4};
   nl_weights<TW, 4>(beta, tau, w, r, om);
@@ -176,12 +210,106 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
   combine2<T>(k, r, om, w, cu);
 }
 
-// Mixed precision: FP32 inputs and polynomial, but the coefficients that
-// enter the smoothness indicators, the indicators and the nonlinear weights
-// in FP64 (their epsilon-sensitive differences are where FP32 cancels).  The
-// inputs are widened exactly on the integer ALU and the weights narrowed
-// (round to nearest) the same way: the hardware conversions would issue on
-// the FP64 pipe, which bounds this path.
+// Mixed precision, Steps 2-3 for one field: FP64 smoothness indicators and
+// nonlinear weights of the FP32 stencil values q, returned narrowed to FP32
+// (r = omega_0 / gamma_0, om[1..4]).
+//  * The indicator uses c_1..c_14 only, each c_l = u_l / den_l with u_l an
+//    integer-weighted sum of the centre-shifted averages and the moments;
+//    the 1/den_l^2 factors are folded into beta_0's weights (m! n!)^2:
+//    576 beta_0 = u1^2 + u2^2 + u3^2 + u5^2 + 9 u4^2 + 144 (u7^2 + u8^2)
+//                 + 51.84 (u6^2 + u9^2) + 1296 (u11^2 + u13^2)
+//                 + 20736 (u10^2 + u14^2) + 576 u12^2.
+//  * The inputs are widened exactly on the integer ALU; the differences
+//    q_k - q5 are taken in FP32 when that is exact for all 32 lanes (checked
+//    with Knuth's TwoSum error term), else in FP64.
+//  * beta_m, tau and a_m = tau^2 / (beta_m + eps) in FP64 (the reciprocal by
+//    rcp_newton); a_m rounded to FP32 and the normalisation of
+//    w~_m = gamma_m (1 + a_m) in FP32: every term is positive, so it adds
+//    no more than a few FP32 ulp to the weights, which are FP32 anyway.
+__device__ __forceinline__ void weights2_ind64(const float* q, const WeightsT<double>& w, const WeightsT<float>& wf,
+                                               float& r, float* om) {
+  const float q5f = q[4];
+  float d32[9];
+  bool exact = true;
+#pragma unroll
+  for (int s = 0; s < 9; ++s) {
+    if (s == 4) continue;
+    const float a = q[s], b = -q5f;
+    const float sum = a + b, bb = sum - a;
+    exact = exact && ((a - (sum - bb)) + (b - bb)) == 0.0f;
+    d32[s] = sum;
+  }
+  double d[9];
+  if (__all_sync(HW_FULL_MASK, exact)) {
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+      if (s != 4) d[s] = widen_f32(d32[s]);
+  } else {
+    const double q5 = widen_f32(q5f);
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+      if (s != 4) d[s] = widen_f32(q[s]) - q5;
+  }
+  const double d1 = d[0], d2 = d[1], d3 = d[2], d4 = d[3], d6 = d[5], d7 = d[6], d8 = d[7], d9 = d[8];
+  const double q10 = widen_f32(q[9]), q11 = widen_f32(q[10]), q12 = widen_f32(q[11]), q13 = widen_f32(q[12]);
+  const double q14 = widen_f32(q[13]), q15 = widen_f32(q[14]), q16 = widen_f32(q[15]), q17 = widen_f32(q[16]);
+  const double s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
+  const double sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
+  const double ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
+  const double s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
+  const double s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
+  const double u1 = 2.0 * ax + 19.0 * dxe - 6.0 * s1011 + 3.0 * s1213;
+  const double u2 = 2.0 * ay + 19.0 * dye + 3.0 * s1415 - 6.0 * s1617;
+  const double u3 = 2.0 * ey - sc + 62.0 * ex - 18.0 * m1110;
+  const double u5 = 2.0 * ex - sc + 62.0 * ey - 18.0 * m1716;
+  const double u4 = 3.0 * cx + 5.0 * (m1213 + m1415);
+  const double u6 = 4.0 * (s1011 - dxe) - ax - 2.0 * s1213;
+  const double u9 = 4.0 * (s1617 - dye) - ay - 2.0 * s1415;
+  const double u7 = ay + 2.0 * dye, u8 = ax + 2.0 * dxe;
+  const double u10 = m1110 - 2.0 * ex, u14 = m1716 - 2.0 * ey;
+  const double u11 = cx + 2.0 * m1213, u13 = cx + 2.0 * m1415;
+  const double u12 = sc - 2.0 * (ex + ey);
+  double b0;
+  if (w.typical) {  // the Jiang-Shu form needs the scaled coefficients c_l = u_l / den_l
+    const double c[15] = {0.0,         u1 * (1.0 / 24.0), u2 * (1.0 / 24.0), u3 * (1.0 / 48.0), -0.125 * u4,
+                          u5 * (1.0 / 48.0), 0.05 * u6,   -0.25 * u7,        -0.25 * u8,        0.05 * u9,
+                          0.25 * u10,  0.25 * u11,        0.25 * u12,        0.25 * u13,        0.25 * u14};
+    b0 = beta_typical_2d(c);
+  } else {
+    double acc = u1 * u1 + u2 * u2 + u3 * u3 + u5 * u5 + 9.0 * u4 * u4;
+    acc += 144.0 * (u7 * u7 + u8 * u8) + 51.84 * (u6 * u6 + u9 * u9);
+    acc += 1296.0 * (u11 * u11 + u13 * u13) + 20736.0 * (u10 * u10 + u14 * u14) + 576.0 * u12 * u12;
+    b0 = acc * (1.0 / 576.0);
+  }
+  const double w2 = d4 * d4, e2 = d6 * d6, s2 = d2 * d2, n2 = d8 * d8;  // dW, dE, dS, dN squared
+  const double b1 = w2 + s2, b2 = e2 + s2, b3 = e2 + n2, b4 = w2 + n2;
+  const double tau = 0.25 * ((fabs(b0 - b1) + fabs(b0 - b2)) + (fabs(b0 - b3) + fabs(b0 - b4)));
+  // the epsilon-sensitive part in FP64: a_m = tau^2 / (beta_m^{1|2} + eps)
+  const double t2 = tau * tau;
+  const double beta[5] = {b0, b1, b2, b3, b4};
+  float a[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const double dm = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
+    a[m] = narrow_f64_ftz(t2 * rcp_newton(dm));
+  }
+  // w~_m = gamma_m (1 + a_m) and the normalisation (well conditioned: all
+  // terms positive) in FP32
+  float e[5], sum = 0.0f;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    e[m] = wf.g[m] * (1.0f + a[m]);
+    sum += e[m];
+  }
+  const float inv = rcp_approx(sum);
+  r = (1.0f + a[0]) * inv;
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) om[m] = e[m] * inv;
+}
+
+// Mixed precision: FP32 inputs and polynomial, the smoothness indicators and
+// nonlinear weights in FP64 (their epsilon-sensitive differences are where
+// FP32 cancels): weights2_ind64.
 __device__ __forceinline__ void recon2_w64(const float* q, const WeightsT<float>& w, const WeightsT<double>& w64,
                                            bool lin, float* cu) {
   Coef2<float> k;
@@ -191,14 +319,9 @@ __device__ __forceinline__ void recon2_w64(const float* q, const WeightsT<float>
     for (int l = 0; l < 15; ++l) cu[l] = k.c[l];
     return;
   }
-  Coef2<double> k64;
-  coef2<double, float, false>(q, k64);
-  double r64, om64[5];
-  weights2<double, false>(k64, w64, r64, om64, nullptr);
-  float om[5];
-#pragma unroll
-  for (int m = 1; m <= 4; ++m) om[m] = narrow_f64(om64[m]);
-  combine2<float>(k, narrow_f64(r64), om, w, cu);
+  float r, om[5];
+  weights2_ind64(q, w64, w, r, om);
+  combine2<float>(k, r, om, w, cu);
 }
 
 // Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)

@@ -14,7 +14,30 @@ struct WeightParams {
   double eps;
   int pow2;
   int linear;
+  int typical;   // 1: Jiang-Shu integral indicator for p0
+  // the same in FP32, rounded on the host: FP32 kernels read these
+  // parameters directly (a conversion re-done at every use would issue on
+  // the FP64 pipe)
+  float gf[5];
+  float inv_g0f;
+  float epsf;
 };
+
+// The scheme constants of a configuration, in both precisions.
+inline WeightParams weight_params(const hweno_config& c) {
+  WeightParams w{};
+  for (int m = 0; m < 5; ++m) {
+    w.g[m] = c.lin_w[m];
+    w.gf[m] = (float)c.lin_w[m];
+  }
+  w.eps = c.eps;
+  w.epsf = (float)c.eps;
+  w.inv_g0f = (float)(1.0 / c.lin_w[0]);
+  w.pow2 = c.weight_pow == 2;
+  w.linear = c.linear_weights != 0;
+  w.typical = c.smoothness == HWENO_BETA_TYPICAL;
+  return w;
+}
 
 // Device-resident time-stepping state of one problem instance.  alpha of
 // the step in progress is (ax, ay); stage 3 accumulates the next step's
@@ -26,6 +49,7 @@ struct Ctl {
   unsigned long long amax_x, amax_y;
   int steps, max_steps, done, last, err;
   int pad;
+  float dtf, axf, ayf, fpad;  // dt, ax, ay rounded to FP32 for the FP32 kernels
 };
 
 // One 1D instance inside the concatenated field planes.

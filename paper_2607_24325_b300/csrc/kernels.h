@@ -29,6 +29,23 @@ struct Stage1Args {
 };
 
 // Arguments of one 2D stage launch.
+// The scalar parameters of the 2D stage in FP32, rounded on the host (the
+// FP32 kernels use these directly: a double-to-float conversion re-done at
+// every use would issue on the FP64 pipe).
+struct Stage2F32 {
+  float ax_op, ay_op, gamma_gas, adv_x, adv_y;
+  float idx, idy, dyx, dxy;   // 1/dx, 1/dy, dy/dx, dx/dy
+};
+inline Stage2F32 stage2_f32(const Grid2& g, double ax_op, double ay_op, double gamma_gas, double adv_x,
+                            double adv_y) {
+  Stage2F32 f;
+  f.ax_op = (float)ax_op; f.ay_op = (float)ay_op; f.gamma_gas = (float)gamma_gas;
+  f.adv_x = (float)adv_x; f.adv_y = (float)adv_y;
+  f.idx = (float)(1.0 / g.dx); f.idy = (float)(1.0 / g.dy);
+  f.dyx = (float)(g.dy / g.dx); f.dxy = (float)(g.dx / g.dy);
+  return f;
+}
+
 struct Stage2Args {
   const void* in;
   const void* base;
@@ -40,6 +57,7 @@ struct Stage2Args {
   int stage;
   double gamma_gas, adv_x, adv_y;
   WeightParams wp;
+  Stage2F32 f32;
   long long plane;        // nx * ny
   const unsigned char* smooth;  // learned indicator: 1 = linear path allowed (nullptr: off)
 };

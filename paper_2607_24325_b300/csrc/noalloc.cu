@@ -147,11 +147,7 @@ extern "C" hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const voi
   e = cudaGetLastError();
   if (e != cudaSuccess) return hw::report_error(HWENO_ERR_CUDA, cudaGetErrorString(e));
 
-  hw::WeightParams wp{};
-  for (int m = 0; m < 5; ++m) wp.g[m] = cfg->lin_w[m];
-  wp.eps = cfg->eps;
-  wp.pow2 = cfg->weight_pow == 2;
-  wp.linear = cfg->linear_weights != 0;
+  const hw::WeightParams wp = hw::weight_params(*cfg);
   const void* ins[3] = {U_in, A, B};
   void* outs[3] = {A, B, U_out};
   for (int s = 1; s <= 3; ++s) {

@@ -173,16 +173,7 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
   T* __restrict__ hat = static_cast<T*>(a.hat);
   const Grid2& G = a.grid;
   const long long plane = a.plane;
-  double dt = 0.0, axd, ayd;
-  if (a.stage == 0) {
-    axd = a.ax_op;
-    ayd = a.ay_op;
-  } else {
-    if (a.ctl->done) return;
-    dt = a.ctl->dt;
-    axd = a.ctl->ax;
-    ayd = a.ctl->ay;
-  }
+  if (a.stage != 0 && a.ctl->done) return;
   const WeightsT<T> wx = make_weights<T>(a.wp);
   WeightsT<T> wy = wx;  // transposed frame: S2 <-> S4
   wy.g[2] = wx.g[4];
@@ -193,12 +184,26 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
   wy64.g[4] = wx64.g[2];
   const bool lin_all = a.wp.linear != 0;
   const unsigned char* __restrict__ smooth = a.smooth;
-  const T g = (T)a.gamma_gas;
-  const T idx = (T)(1.0 / G.dx), idy = (T)(1.0 / G.dy);
-  const T dyx = (T)(G.dy / G.dx), dxy = (T)(G.dx / G.dy);
-  const T tdt = (T)dt;
-  // converted once: a double -> float conversion runs on the narrow FP64 pipe
-  const T ax_t = (T)axd, ay_t = (T)ayd, advx_t = (T)a.adv_x, advy_t = (T)a.adv_y;
+  // scalars in T; the FP32 kernels take the host-rounded FP32 copies (a
+  // conversion the compiler re-did at each use would run on the FP64 pipe)
+  T g, idx, idy, dyx, dxy, tdt, ax_t, ay_t, advx_t, advy_t;
+  if constexpr (sizeof(T) == 4) {
+    g = a.f32.gamma_gas; idx = a.f32.idx; idy = a.f32.idy; dyx = a.f32.dyx; dxy = a.f32.dxy;
+    advx_t = a.f32.adv_x; advy_t = a.f32.adv_y;
+    if (a.stage == 0) {
+      tdt = T(0); ax_t = a.f32.ax_op; ay_t = a.f32.ay_op;
+    } else {
+      tdt = a.ctl->dtf; ax_t = a.ctl->axf; ay_t = a.ctl->ayf;
+    }
+  } else {
+    g = a.gamma_gas; idx = 1.0 / G.dx; idy = 1.0 / G.dy; dyx = G.dy / G.dx; dxy = G.dx / G.dy;
+    advx_t = a.adv_x; advy_t = a.adv_y;
+    if (a.stage == 0) {
+      tdt = T(0); ax_t = a.ax_op; ay_t = a.ay_op;
+    } else {
+      tdt = a.ctl->dt; ax_t = a.ctl->ax; ay_t = a.ctl->ay;
+    }
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int tiles_x = (G.nx + kT2 - 1) / kT2;
@@ -266,7 +271,7 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
         Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
       }
       if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
-        const int sidx = r * kSP + lane - 1;
+        const int sidx = stash_at<T>(r, lane - 1);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           stash[(0 * NC + k) * kSS + sidx] = -(Gu[k] - Fu[k]) * idx;
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
       }
       const int j = j0 - 1 + lane;
       if (lane >= 1 && lane <= kT2 && j < G.ny) {
-        const int sidx = (lane - 1) * kSP + c;
+        const int sidx = stash_at<T>(lane - 1, c);
         const long long p = (long long)j * G.nx + i;
         T nu[NC];
 #pragma unroll

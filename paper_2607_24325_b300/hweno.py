@@ -24,6 +24,7 @@ EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
 BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
 FP64, FP32, FP32_IND64 = 0, 1, 2
 DT_CFL, DT_CFL_DX53 = 0, 1
+BETA_MOMENT, BETA_TYPICAL = 0, 1
 
 # every extern "C" symbol include/hweno.h declares
 EXPORTS = (
@@ -51,6 +52,7 @@ class hweno_config(C.Structure):
         ("lin_w", C.c_double * 5), ("eps", C.c_double), ("weight_pow", C.c_int),
         ("charwise", C.c_int), ("linear_weights", C.c_int), ("cfl", C.c_double), ("dt_rule", C.c_int),
         ("bc", C.c_int * 4), ("bc_state", (C.c_double * 4) * 4), ("precision", C.c_int),
+        ("smoothness", C.c_int),
     ]
 
 
@@ -78,6 +80,7 @@ class Config:
     bc: tuple = (BC_PERIODIC,) * 4
     bc_state: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])
     precision: int = FP64
+    smoothness: int = BETA_MOMENT
 
     @property
     def ncomp(self) -> int:
@@ -101,6 +104,7 @@ class Config:
             c.lin_w[k] = w[k]
         c.eps, c.weight_pow, c.charwise, c.linear_weights = self.eps, self.weight_pow, self.charwise, self.linear_weights
         c.cfl, c.dt_rule, c.precision = self.cfl, self.dt_rule, self.precision
+        c.smoothness = self.smoothness
         for k in range(4):
             c.bc[k] = self.bc[k]
             for q in range(4):

@@ -15,7 +15,7 @@ def cfg_from(prob: oracle.Problem, precision: int = hw.FP64) -> hw.Config:
                      weight_pow=prob.weight_pow, charwise=prob.charwise,
                      linear_weights=prob.linear_weights, cfl=prob.cfl, dt_rule=prob.dt_rule,
                      bc=tuple(prob.bc), bc_state=[list(r) for r in prob.bc_state],
-                     precision=precision)
+                     precision=precision, smoothness=prob.smoothness)
 
 
 def plane_rel_err(got, ref) -> float:

@@ -127,6 +127,57 @@ def test_operator_2d_large_sampled():
     assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
 
 
+# ------------------------------------- Jiang-Shu (typical) indicator variant
+@pytest.mark.parametrize("dim,eq,charwise", [(1, oracle.EQ_ADVECTION, 1), (1, oracle.EQ_EULER, 1),
+                                             (2, oracle.EQ_BURGERS, 1), (2, oracle.EQ_EULER, 1),
+                                             (2, oracle.EQ_EULER, 0)])
+def test_operator_typical_indicator_fp64(dim, eq, charwise):
+    """The smoothness-indicator variant the paper replaces (Eq.
+    smoothness-indicator-typical and its 2D form), FP64, rough data: parity
+    with the oracle, and the switch changes the result."""
+    euler = eq == oracle.EQ_EULER
+    if dim == 1:
+        n = 203
+        U = W.random_state(1, (n,), seed=41 + eq, euler=euler)
+        kw = dict(dim=1, nx=n, lin_w=(0.6, 0.2, 0.2), bc=(oracle.BC_OUTFLOW, oracle.BC_REFLECT, 0, 0))
+        ax, ay = 2.1, 0.0
+    else:
+        nx, ny = 67, 41
+        U = W.random_state(2, (ny, nx), seed=43 + eq, euler=euler, moment_scale=0.3)
+        kw = dict(dim=2, nx=nx, ny=ny, lin_w=W2D, bc=(0, 0, 1, 2))
+        ax, ay = 2.2, 1.9
+    prob = oracle.Problem(equation=eq, charwise=charwise, smoothness=oracle.BETA_TYPICAL, eps=1e-6, **kw)
+    L, D, Lr, Dr = _operator_pair(prob, U, ax, ay)
+    assert plane_rel_err(L, Lr) < TOL64
+    assert plane_rel_err(D, Dr) < TOL64
+    Lm, _ = oracle.operator(oracle.Problem(equation=eq, charwise=charwise, eps=1e-6, **kw), U, ax, ay)
+    assert plane_rel_err(Lm, Lr) > 1e-6
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_operator_typical_indicator_mixed(dim):
+    """FP32 storage and stencil with FP64 typical indicators, on the
+    FP32-rounded input: within max(2e-5, 100 x the oracle's spread under
+    FP32 unit-roundoff input noise)."""
+    if dim == 1:
+        N = 200
+        prob = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=N, xlo=0, xhi=2,
+                              smoothness=oracle.BETA_TYPICAL)
+        U = W.cells_1d(W.euler_smooth_1d(0.0), 0, 2, N)
+    else:
+        N = 64
+        prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2, lin_w=W2D,
+                              smoothness=oracle.BETA_TYPICAL)
+        U = W.cells_2d(W.euler_smooth_2d(0.0), 0, 2, 0, 2, N, N)
+    U32 = U.astype(np.float32).astype(np.float64)
+    L, D, _, _ = _operator_pair(prob, U32, 2.5, 2.5, precision=hw.FP32_IND64)
+    Lr, Dr, sL, sD = oracle_spread(prob, U32, 2.5, 2.5, rel=2.0 ** -24)
+    ok, e, tol = within_spread(L, Lr, sL, 2e-5)
+    assert ok, (e, tol)
+    ok, e, tol = within_spread(D, Dr, sD, 2e-5)
+    assert ok, (e, tol)
+
+
 # ------------------------------------------------------------ whole runs
 def test_run_1d_advection_config1():
     """1D advection sin(pi x) on [0,2], N = 160, CFL 0.6, to t = 2 (FP64)."""

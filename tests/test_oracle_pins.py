@@ -578,3 +578,115 @@ def test_blast_wave_runs_positive():
     pr = 0.4 * (U[2] - 0.5 * U[1] ** 2 / rho)
     assert t == 0.038 and rho.min() > 0 and pr.min() > 0
     assert abs(U[0].sum() - U0[0].sum()) < 1e-12 * U0[0].sum()
+
+
+# ---------------------------------------------------------------------------
+# Jiang-Shu ("typical") smoothness indicator, Eq. (smoothness-indicator-
+# typical) and its 2D form: the oracle integrates the squared derivatives by
+# Gauss-Legendre quadrature; here the same integrals are taken exactly with
+# rational monomial moments, int_{-1/2}^{1/2} xi^k dxi.
+# ---------------------------------------------------------------------------
+from fractions import Fraction as _Fr  # noqa: E402
+
+
+def _mono_int(k):
+    """Exact int_{-1/2}^{1/2} xi^k dxi."""
+    return _Fr(0) if k % 2 else _Fr(1, 2 ** k * (k + 1))
+
+
+def _falling(n, m):
+    f = 1
+    for j in range(m):
+        f *= (n - j)
+    return f
+
+
+def _beta_typ_1d_exact(c):
+    c = [_Fr(x) for x in c]
+    tot = _Fr(0)
+    for l in range(1, len(c)):
+        d = [(c[k] * _falling(k, l), k - l) for k in range(l, len(c))]   # derivative terms
+        for a, pa in d:
+            for b, pb in d:
+                tot += a * b * _mono_int(pa + pb)
+    return tot
+
+
+_EXP2 = [(0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2), (3, 0), (2, 1), (1, 2), (0, 3), (4, 0), (3, 1),
+         (2, 2), (1, 3), (0, 4)]
+
+
+def _beta_typ_2d_exact(c):
+    c = [_Fr(x) for x in c] + [_Fr(0)] * (15 - len(c))
+    tot = _Fr(0)
+    for l in range(1, 5):
+        for m in range(l + 1):
+            n = l - m
+            d = [(c[i] * _falling(a, m) * _falling(b, n), a - m, b - n)
+                 for i, (a, b) in enumerate(_EXP2) if a >= m and b >= n and c[i] != 0]
+            for x, ax, ay in d:
+                for y, bx, by in d:
+                    tot += x * y * _mono_int(ax + bx) * _mono_int(ay + by)
+    return tot
+
+
+def test_typical_indicator_1d_exact_integrals():
+    """beta_0..beta_2 of the typical indicator equal the exact integrals of
+    the squared derivatives of p0 (quartic) and p1, p2 (linear)."""
+    rng = np.random.default_rng(31)
+    G0, G1, G2 = oracle.coef_maps_1d()
+    prob = oracle.Problem(dim=1, lin_w=(0.6, 0.2, 0.2), smoothness=oracle.BETA_TYPICAL)
+    dx = 0.37
+    for _ in range(5):
+        inp = rng.normal(size=5)
+        r = oracle.recon_cell_1d(prob, inp, dx)
+        d = np.array([inp[0], inp[1], inp[2], dx * inp[3], dx * inp[4]])
+        c0, c1, c2 = G0 @ d, G1 @ inp[:2], G2 @ inp[1:3]
+        ref = [_beta_typ_1d_exact(c0), _beta_typ_1d_exact(c1), _beta_typ_1d_exact(c2)]
+        np.testing.assert_allclose(r["beta"], [float(x) for x in ref], rtol=1e-13, atol=1e-15)
+
+
+def test_typical_indicator_2d_exact_integrals():
+    rng = np.random.default_rng(32)
+    G0, Gm = oracle.coef_maps_2d()
+    prob = oracle.Problem(dim=2, nx=8, ny=8, lin_w=(0.6, 0.1, 0.1, 0.1, 0.1), smoothness=oracle.BETA_TYPICAL)
+    for _ in range(4):
+        q = rng.normal(size=17)
+        r = oracle.recon_cell_2d(prob, q, 0.5, 0.25)
+        ref0 = _beta_typ_2d_exact(G0 @ q)
+        assert abs(r["beta"][0] - float(ref0)) <= 1e-13 * max(1.0, abs(float(ref0)))
+        # the linear p_m: the integral of (sx^2 + sy^2), i.e. the moment form
+        mom = oracle.recon_cell_2d(oracle.Problem(dim=2, nx=8, ny=8, lin_w=prob.lin_w), q, 0.5, 0.25)
+        np.testing.assert_allclose(r["beta"][1:], mom["beta"][1:], rtol=1e-14)
+
+
+def test_typical_indicator_closed_values():
+    """p = xi^2: int (2 xi)^2 + int 2^2 = 1/3 + 4; p = xi eta: int (eta^2 + xi^2) + 1 = 1/6 + 1."""
+    assert _beta_typ_1d_exact([0, 0, 1]) == _Fr(13, 3)
+    assert _beta_typ_2d_exact([0, 0, 0, 0, 1]) == _Fr(7, 6)
+    # and the oracle's quadrature through a reconstruction whose p0 is xi^2:
+    # u = xi^2 sampled as cell averages and derivative moments
+    prob = oracle.Problem(dim=1, lin_w=(0.6, 0.2, 0.2), smoothness=oracle.BETA_TYPICAL)
+    dx = 1.0
+    avg = lambda a: ((a + 0.5) ** 3 - (a - 0.5) ** 3) / 3.0      # mean of x^2 over [a-1/2, a+1/2]
+    inp = [avg(-1.0), avg(0.0), avg(1.0), -2.0, 2.0]              # v = mean of 2x
+    r = oracle.recon_cell_1d(prob, inp, dx)
+    assert abs(r["beta"][0] - 13.0 / 3.0) < 1e-13
+
+
+def test_typical_equals_moment_on_linear_data():
+    """Linear data: p0 is linear, and both indicators reduce to the squared
+    gradient, so the weights are identical."""
+    prob_m = oracle.Problem(dim=2, nx=8, ny=8, lin_w=(0.6, 0.1, 0.1, 0.1, 0.1))
+    prob_t = oracle.Problem(dim=2, nx=8, ny=8, lin_w=(0.6, 0.1, 0.1, 0.1, 0.1), smoothness=oracle.BETA_TYPICAL)
+    ax, ay = 0.7, -1.3
+    q = np.zeros(17)
+    for r_ in range(3):
+        for c_ in range(3):
+            q[r_ * 3 + c_] = ax * (c_ - 1) + ay * (r_ - 1)
+    q[9:13] = ax
+    q[13:17] = ay
+    a = oracle.recon_cell_2d(prob_m, q, 1.0, 1.0)
+    b = oracle.recon_cell_2d(prob_t, q, 1.0, 1.0)
+    np.testing.assert_allclose(a["beta"], b["beta"], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(a["omega"], b["omega"], rtol=1e-13)
