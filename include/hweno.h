@@ -57,7 +57,8 @@ typedef enum {
 } hweno_status;
 
 enum { HWENO_EQ_ADVECTION = 0, HWENO_EQ_BURGERS = 1, HWENO_EQ_EULER = 2 };
-enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECT = 2, HWENO_BC_INFLOW = 3 };
+enum { HWENO_BC_PERIODIC = 0, HWENO_BC_OUTFLOW = 1, HWENO_BC_REFLECT = 2, HWENO_BC_INFLOW = 3,
+       HWENO_BC_SPLIT = 4, HWENO_BC_SHOCK = 5 };
 enum { HWENO_FP64 = 0, HWENO_FP32 = 1, HWENO_FP32_IND64 = 2 };
 enum { HWENO_DT_CFL = 0, HWENO_DT_CFL_DX53 = 1 };
 enum { HWENO_BETA_MOMENT = 0, HWENO_BETA_TYPICAL = 1 };
@@ -82,6 +83,15 @@ enum { HWENO_BETA_MOMENT = 0, HWENO_BETA_TYPICAL = 1 };
  *                 cfl / (alpha_x/hx + alpha_y/hy)
  *  bc[4]          x-low, x-high, y-low, y-high: HWENO_BC_*
  *  bc_state[4][4] conservative state imposed by HWENO_BC_INFLOW sides
+ *                 (ghost derivative moments zero)
+ *  HWENO_BC_SPLIT and HWENO_BC_SHOCK (2D only) decide per ghost cell by the
+ *  coordinate s of its centre along the side (x on the y sides, y on the x
+ *  sides) and the time t of the RK stage (t^n, t^n + dt, t^n + dt/2):
+ *    SPLIT: s < bc_param[side][0] -> bc_state[side], else reflective --
+ *           the wall of the double Mach reflection example (Sec. 3);
+ *    SHOCK: s < bc_param[side][0] + bc_param[side][1] t -> bc_state[side],
+ *           else bc_state2[side] -- a straight shock moving along the side
+ *           (that example's top boundary).
  *  precision      HWENO_FP64, HWENO_FP32 (storage and stencil arithmetic), or
  *                 HWENO_FP32_IND64 (FP32 storage and stencil arithmetic; the
  *                 coefficients entering the smoothness indicators, the
@@ -111,6 +121,8 @@ typedef struct {
   double bc_state[4][4];
   int precision;
   int smoothness;
+  double bc_state2[4][4];
+  double bc_param[4][2];
 } hweno_config;
 
 typedef struct hweno_solver hweno_solver;
@@ -165,11 +177,13 @@ hweno_status hweno_alpha(hweno_solver* s, double* alpha_x, double* alpha_y);
  * given Lax-Friedrichs constants: L_out[nf][cells] = (L^u, L^v, L^w) of Eq.
  * semi-discrete-scheme / 2D-semi-discrete-scheme-uniform, dhat_out[nc*dim]
  * [cells] = the limited derivatives v-hat (and w-hat) of Step 3.  Both are
- * caller device buffers of the solver's element type. */
+ * caller device buffers of the solver's element type.  Time-dependent
+ * boundaries take the solver's current time. */
 hweno_status hweno_apply_operator(hweno_solver* s, double alpha_x, double alpha_y,
                                   void* L_out, void* dhat_out);
 
-/* One SSP-RK3 step (Step 4) with the given dt and Lax-Friedrichs constants. */
+/* One SSP-RK3 step (Step 4) with the given dt and Lax-Friedrichs constants,
+ * from the solver's current time, which it advances by dt. */
 hweno_status hweno_step(hweno_solver* s, double dt, double alpha_x, double alpha_y);
 
 /* Advance to t_final with the device-resident CFL time step (alpha from the

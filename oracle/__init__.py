@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "hweno_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
-BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW, BC_SPLIT, BC_SHOCK = 0, 1, 2, 3, 4, 5
 DT_CFL, DT_CFL_DX53 = 0, 1
 BETA_MOMENT, BETA_TYPICAL = 0, 1
 
@@ -50,7 +50,8 @@ class _Problem(C.Structure):
         ("lin_w", C.c_double * 5), ("eps", C.c_double),
         ("weight_pow", C.c_int), ("charwise", C.c_int), ("linear_weights", C.c_int),
         ("dt_rule", C.c_int), ("bc", C.c_int * 4), ("bc_state", (C.c_double * 4) * 4),
-        ("cfl", C.c_double), ("smoothness", C.c_int),
+        ("cfl", C.c_double), ("bc_state2", (C.c_double * 4) * 4), ("bc_param", (C.c_double * 2) * 4),
+        ("t", C.c_double), ("smoothness", C.c_int),
     ]
 
 
@@ -78,6 +79,9 @@ class Problem:
     bc_state: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])
     cfl: float = 0.6
     smoothness: int = BETA_MOMENT  # BETA_TYPICAL: the Jiang-Shu integral indicator
+    bc_state2: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])  # BC_SHOCK second state
+    bc_param: list = field(default_factory=lambda: [[0.0, 0.0] for _ in range(4)])  # BC_SPLIT / BC_SHOCK
+    t: float = 0.0  # time of the state (time-dependent boundaries)
 
     @property
     def ncomp(self) -> int:
@@ -120,6 +124,12 @@ class Problem:
                 s.bc_state[k][c] = self.bc_state[k][c]
         s.cfl = self.cfl
         s.smoothness = self.smoothness
+        for k in range(4):
+            for c in range(4):
+                s.bc_state2[k][c] = self.bc_state2[k][c]
+            for c in range(2):
+                s.bc_param[k][c] = self.bc_param[k][c]
+        s.t = self.t
         return s
 
 

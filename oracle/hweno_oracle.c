@@ -546,14 +546,26 @@ static double mirror_sign(const or_problem* p, int d, int k, int axis) {
   return s;
 }
 
-/* Fill the ghosts of one line along `axis` (0: x, 1: y) at fixed other index. */
+/* Fill the ghosts of one line along `axis` (0: x, 1: y) at fixed other index.
+ * The split and moving-shock sides decide by the line's centre coordinate
+ * along the side (y of the row for x sides, x of the column for y sides). */
 static void fill_line(const or_problem* p, padded_t* P, int axis, int other) {
   const int n = axis == 0 ? P->nx : P->ny;
+  const double along = axis == 0 ? p->ylo + (other + 0.5) * (p->yhi - p->ylo) / (p->dim == 2 ? p->ny : 1)
+                                 : p->xlo + (other + 0.5) * (p->xhi - p->xlo) / p->nx;
   for (int f = 0; f < P->nf; ++f) {
     const int d = f / P->nc, k = f % P->nc;
 #define AT(t) (*(axis == 0 ? pcell(P, f, (t), other) : pcell(P, f, other, (t))))
     for (int side = 0; side < 2; ++side) {
-      const int bc = p->bc[2 * axis + side];
+      const int sd = 2 * axis + side;
+      int bc = p->bc[sd];
+      const double* state = p->bc_state[sd];
+      if (bc == OR_BC_SPLIT) {
+        bc = along < p->bc_param[sd][0] ? OR_BC_INFLOW : OR_BC_REFLECT;
+      } else if (bc == OR_BC_SHOCK) {
+        bc = OR_BC_INFLOW;
+        if (!(along < p->bc_param[sd][0] + p->bc_param[sd][1] * p->t)) state = p->bc_state2[sd];
+      }
       for (int r = 0; r < 2; ++r) {
         const int g = side == 0 ? -1 - r : n + r;
         double val;
@@ -564,7 +576,7 @@ static void fill_line(const or_problem* p, padded_t* P, int axis, int other) {
         } else if (bc == OR_BC_REFLECT) {
           val = mirror_sign(p, d, k, axis) * AT(side == 0 ? r : n - 1 - r);
         } else {
-          val = d == 0 ? p->bc_state[2 * axis + side][k] : 0.0;
+          val = d == 0 ? state[k] : 0.0;
         }
         AT(g) = val;
       }
@@ -832,6 +844,10 @@ static int check_problem(const or_problem* p) {
   const int nlin = p->dim == 1 ? 3 : 5;
   for (int m = 0; m < nlin; ++m)
     if (!(p->lin_w[m] > 0.0)) return -1;
+  for (int sd = 0; sd < 4; ++sd) {
+    if (p->bc[sd] < OR_BC_PERIODIC || p->bc[sd] > OR_BC_SHOCK) return -1;
+    if (p->dim == 1 && p->bc[sd] >= OR_BC_SPLIT) return -1; /* need a coordinate along the side */
+  }
   return 0;
 }
 
@@ -886,16 +902,20 @@ int or_step(const or_problem* p, double* U, double dt, double ax, double ay) {
   int rc = -1;
   if (!U0 || !Us || !L || !H0 || !Hs) goto done;
   memcpy(U0, U, sizeof(double) * nall);
+  /* boundary values at the stage times t^n, t^n + dt, t^n + dt/2 */
+  or_problem ps = *p;
   /* stage 1: u(1) = u-hat^n + dt L(u^n) */
-  if (or_operator(p, U0, ax, ay, L, H0)) goto done;
+  if (or_operator(&ps, U0, ax, ay, L, H0)) goto done;
   for (size_t c = 0; c < nu; ++c) Us[c] = U0[c] + dt * L[c];
   for (size_t c = 0; c < nd; ++c) Us[nu + c] = H0[c] + dt * L[nu + c];
   /* stage 2: u(2) = 3/4 u-hat^n + 1/4 (u-hat(1) + dt L(u(1))) */
-  if (or_operator(p, Us, ax, ay, L, Hs)) goto done;
+  ps.t = p->t + dt;
+  if (or_operator(&ps, Us, ax, ay, L, Hs)) goto done;
   for (size_t c = 0; c < nu; ++c) Us[c] = 0.75 * U0[c] + 0.25 * (Us[c] + dt * L[c]);
   for (size_t c = 0; c < nd; ++c) Us[nu + c] = 0.75 * H0[c] + 0.25 * (Hs[c] + dt * L[nu + c]);
   /* stage 3: u^{n+1} = 1/3 u-hat^n + 2/3 (u-hat(2) + dt L(u(2))) */
-  if (or_operator(p, Us, ax, ay, L, Hs)) goto done;
+  ps.t = p->t + 0.5 * dt;
+  if (or_operator(&ps, Us, ax, ay, L, Hs)) goto done;
   for (size_t c = 0; c < nu; ++c) U[c] = U0[c] / 3.0 + 2.0 / 3.0 * (Us[c] + dt * L[c]);
   for (size_t c = 0; c < nd; ++c) U[nu + c] = H0[c] / 3.0 + 2.0 / 3.0 * (Hs[c] + dt * L[nu + c]);
   rc = 0;
@@ -908,7 +928,8 @@ int or_run(const or_problem* p, double* U, double t_final, int max_steps, double
            int* steps_out) {
   if (check_problem(p)) return -1;
   const size_t nall = (size_t)p->nx * (p->dim == 2 ? p->ny : 1) * or_nfields(p);
-  double t = 0.0;
+  or_problem ps = *p;
+  double t = p->t;
   int steps = 0, rc = 0;
   while (t < t_final && steps < max_steps) {
     double ax, ay;
@@ -916,7 +937,8 @@ int or_run(const or_problem* p, double* U, double t_final, int max_steps, double
     double dt = or_dt(p, ax, ay);
     if (!(dt > 0.0)) { rc = -2; break; }
     if (t + dt >= t_final) dt = t_final - t;
-    if (or_step(p, U, dt, ax, ay)) { rc = -1; break; }
+    ps.t = t;
+    if (or_step(&ps, U, dt, ax, ay)) { rc = -1; break; }
     ++steps;
     t = (t_final - (t + dt) <= 1e-15 * fabs(t_final)) ? t_final : t + dt;
     for (size_t c = 0; c < nall; ++c)

@@ -27,7 +27,16 @@ extern "C" {
 #endif
 
 enum { OR_EQ_ADVECTION = 0, OR_EQ_BURGERS = 1, OR_EQ_EULER = 2 };
-enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECT = 2, OR_BC_INFLOW = 3 };
+enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1, OR_BC_REFLECT = 2, OR_BC_INFLOW = 3,
+       OR_BC_SPLIT = 4, OR_BC_SHOCK = 5 };
+/* OR_BC_SPLIT: ghost cells whose centre lies, along the side, below
+ *   bc_param[side][0] take bc_state[side] (zero moments), the others mirror
+ *   (OR_BC_REFLECT) -- the double Mach reflection wall (Sec. 3, the double
+ *   Mach reflection example: post-shock state for x < 1/6, reflective after).
+ * OR_BC_SHOCK: ghost cells whose centre lies, along the side, below
+ *   bc_param[side][0] + bc_param[side][1] t take bc_state[side], the others
+ *   bc_state2[side] (zero moments) -- a straight shock moving along the side
+ *   (the same example's top boundary).  t is the time of the RK stage. */
 enum { OR_DT_CFL = 0, OR_DT_CFL_DX53 = 1 };
 
 typedef struct {
@@ -46,6 +55,9 @@ typedef struct {
   int bc[4];                /* x-low, x-high, y-low, y-high: OR_BC_* */
   double bc_state[4][4];    /* conservative state used by OR_BC_INFLOW sides */
   double cfl;
+  double bc_state2[4][4];   /* second state of OR_BC_SHOCK sides */
+  double bc_param[4][2];    /* OR_BC_SPLIT: (split position, -); OR_BC_SHOCK: (x0, speed) */
+  double t;                 /* time of the state (time-dependent boundaries) */
   int smoothness;           /* OR_BETA_MOMENT: Step 2's indicator (the paper's);
                                OR_BETA_TYPICAL: the Jiang-Shu integral indicator that
                                Step 2 replaces, Eq. (smoothness-indicator-typical[-2D]) */

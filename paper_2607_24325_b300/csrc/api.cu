@@ -77,8 +77,11 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
   if (c->precision != HWENO_FP64 && c->precision != HWENO_FP32 && c->precision != HWENO_FP32_IND64)
     return fail(HWENO_ERR_ARG, "bad precision");
   const int nsides = c->dim == 1 ? 2 : 4;
-  for (int k = 0; k < nsides; ++k)
-    if (c->bc[k] < 0 || c->bc[k] > 3) return fail(HWENO_ERR_ARG, "bad boundary condition on side %d", k);
+  for (int k = 0; k < nsides; ++k) {
+    if (c->bc[k] < 0 || c->bc[k] > HWENO_BC_SHOCK) return fail(HWENO_ERR_ARG, "bad boundary condition on side %d", k);
+    if (c->dim == 1 && c->bc[k] >= HWENO_BC_SPLIT)
+      return fail(HWENO_ERR_ARG, "split and moving-shock boundaries need a 2D grid (side %d)", k);
+  }
   for (int a = 0; a < c->dim; ++a)
     if ((c->bc[2 * a] == HWENO_BC_PERIODIC) != (c->bc[2 * a + 1] == HWENO_BC_PERIODIC))
       return fail(HWENO_ERR_ARG, "periodic boundaries must be paired (axis %d)", a);
@@ -199,10 +202,17 @@ struct Engine {
       grid.ny = cfg.ny;
       for (int q = 0; q < 4; ++q) {
         grid.bc[q] = cfg.bc[q];
-        for (int r = 0; r < 4; ++r) grid.st[q][r] = cfg.bc_state[q][r];
+        for (int r = 0; r < 4; ++r) {
+          grid.st[q][r] = cfg.bc_state[q][r];
+          grid.st2[q][r] = cfg.bc_state2[q][r];
+        }
+        grid.bcp[q][0] = cfg.bc_param[q][0];
+        grid.bcp[q][1] = cfg.bc_param[q][1];
       }
       grid.dx = (cfg.xhi - cfg.xlo) / cfg.nx;
       grid.dy = (cfg.yhi - cfg.ylo) / cfg.ny;
+      grid.xlo = cfg.xlo;
+      grid.ylo = cfg.ylo;
       cells = (long long)cfg.nx * cfg.ny;
       offsets = {0, cells};
       hw::Ctl& C = ctl_init[0];
@@ -283,7 +293,7 @@ struct Engine {
 
   hweno_status run_indicator() {
     hw::MlpDev m{mlp_w, mlp_w + 32 * 80, mlp_bias, z_thresh};
-    HW_CK(hw::launch_mlp_infer2d(prec, cfg.equation, S, grid, cells, m, troubled, smooth, num_sms, own));
+    HW_CK(hw::launch_mlp_infer2d(prec, cfg.equation, S, grid, cells, m, ctl, troubled, smooth, num_sms, own));
     return HWENO_OK;
   }
 
@@ -426,10 +436,13 @@ struct Engine {
     if (!(dt >= 0.0) || !std::isfinite(dt) || !(ax >= 0.0) || !(ay >= 0.0))
       return fail(HWENO_ERR_ARG, "dt and alpha must be finite and non-negative");
     HW_TRY(enter());
-    HW_CK(cudaStreamSynchronize(own));
+    HW_TRY(read_ctl());
+    std::vector<double> t_now(n_inst);
+    for (int k = 0; k < n_inst; ++k) t_now[k] = ctl_host[k].t;
     if (learned) HW_TRY(run_indicator());
     for (int k = 0; k < n_inst; ++k) {
       ctl_host[k] = ctl_init[k];
+      ctl_host[k].t = t_now[k];
       ctl_host[k].dt = dt;
       ctl_host[k].ax = ax;
       ctl_host[k].ay = ay;
@@ -441,7 +454,10 @@ struct Engine {
     HW_CK(cudaMemcpyAsync(ctl_manual, ctl_host, sizeof(hw::Ctl) * n_inst, cudaMemcpyHostToDevice, own));
     HW_TRY(rk_stages(ctl_manual));
     HW_CK(cudaStreamSynchronize(own));
-    // the new state's alpha for the next advance
+    // the solver's time moves by dt; the new state's alpha for the next advance
+    HW_TRY(read_ctl());
+    for (int k = 0; k < n_inst; ++k) ctl_host[k].t = t_now[k] + dt;
+    HW_CK(cudaMemcpyAsync(ctl, ctl_host, sizeof(hw::Ctl) * n_inst, cudaMemcpyHostToDevice, own));
     HW_TRY(alpha_init());
     return leave();
   }
@@ -791,7 +807,7 @@ hweno_status hweno_indicator_features(hweno_solver* s, float* feat_out) {
   if (e.dim != 2) return fail(HWENO_ERR_ARG, "the learned indicator serves 2D solvers");
   if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
   HW_TRY(e.enter());
-  HW_CK(hw::launch_features2d(e.prec, e.cfg.equation, e.S, e.grid, e.cells, feat_out, e.num_sms, e.own));
+  HW_CK(hw::launch_features2d(e.prec, e.cfg.equation, e.S, e.grid, e.cells, e.ctl, feat_out, e.num_sms, e.own));
   return e.leave();
 }
 
@@ -802,7 +818,7 @@ hweno_status hweno_indicator_labels(hweno_solver* s, float* dev_out) {
   if (!e.has_state) return fail(HWENO_ERR_STATE, "no state set");
   HW_TRY(e.enter());
   HW_CK(hw::launch_labels2d(e.prec, e.cfg.equation, e.cfg.charwise, e.S, e.grid, e.cells, e.wp, e.cfg.gamma_gas,
-                            dev_out, e.num_sms, e.own));
+                            e.ctl, dev_out, e.num_sms, e.own));
   return e.leave();
 }
 

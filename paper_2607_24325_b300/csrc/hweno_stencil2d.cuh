@@ -48,18 +48,41 @@ __device__ constexpr int frame_field(int d, int k) {
   return (d == 0 ? 0 : (D == 0 ? d : 3 - d)) * NC + frame_comp<D, EQ>(k);
 }
 
+// The rule a side applies to one ghost cell: split walls and moving shocks
+// resolve, by the coordinate `along` of the ghost cell's centre along the
+// side and the stage time t, into an inflow state or a mirror.
+struct SideRule {
+  int bc;
+  const double* st;
+};
+__device__ __forceinline__ SideRule side_rule(const Grid2& G, int sd, double along, double t) {
+  SideRule r{G.bc[sd], G.st[sd]};
+  if (r.bc == HWENO_BC_SPLIT) {
+    r.bc = along < G.bcp[sd][0] ? HWENO_BC_INFLOW : HWENO_BC_REFLECT;
+  } else if (r.bc == HWENO_BC_SHOCK) {
+    r.bc = HWENO_BC_INFLOW;
+    if (!(along < G.bcp[sd][0] + G.bcp[sd][1] * t)) r.st = G.st2[sd];
+  }
+  return r;
+}
+
 // Value of field f at cell (i, j), ghost cells resolved as "x sides for the
-// interior rows, then y sides for every column".
+// interior rows, then y sides for every column"; t is the time the
+// time-dependent sides are evaluated at.
 template <typename T, int EQ, int NC>
 __device__ __forceinline__ T load_ghost2(const T* __restrict__ in, long long plane, const Grid2& G,
-                                         int f, int i, int j) {
+                                         int f, int i, int j, double t) {
   const int d = f / NC, k = f % NC;
-  const GhostMap gx = ghost_map(i, G.nx, G.bc[0], G.bc[1]);
-  const GhostMap gy = ghost_map(j, G.ny, G.bc[2], G.bc[3]);
-  if (gy.fixed) return d == 0 ? (T)G.st[2 + gy.side][k] : T(0);
+  const double xc = G.xlo + (i + 0.5) * G.dx;   // the column's centre (y sides)
+  const SideRule ry0 = side_rule(G, 2, xc, t), ry1 = side_rule(G, 3, xc, t);
+  const GhostMap gy = ghost_map(j, G.ny, ry0.bc, ry1.bc);
+  if (gy.fixed) return d == 0 ? (T)(gy.side ? ry1.st : ry0.st)[k] : T(0);
+  const double yc = G.ylo + (gy.src + 0.5) * G.dy;  // the source row's centre (x sides)
+  const SideRule rx0 = side_rule(G, 0, yc, t), rx1 = side_rule(G, 1, yc, t);
+  const GhostMap gx = ghost_map(i, G.nx, rx0.bc, rx1.bc);
   T v;
   if (gx.fixed) {
-    v = d == 0 ? (T)G.st[gx.side][k] : T(0);
+    v = d == 0 ? (T)(gx.side ? rx1.st : rx0.st)[k] : T(0);
   } else {
     v = in[f * plane + (long long)gy.src * G.nx + gx.src];
     if (gx.flip && mirror_negates(EQ, d, k, 0)) v = -v;

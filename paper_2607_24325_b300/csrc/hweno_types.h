@@ -67,7 +67,10 @@ struct Grid2 {
   int nx, ny;
   int bc[4];
   double dx, dy;
+  double xlo, ylo;
   double st[4][4];
+  double st2[4][4];   // second state of HWENO_BC_SHOCK sides
+  double bcp[4][2];   // HWENO_BC_SPLIT / HWENO_BC_SHOCK parameters
 };
 
 }  // namespace hw

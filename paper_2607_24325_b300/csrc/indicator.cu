@@ -55,7 +55,8 @@ __device__ __forceinline__ float feature(F at, int k, float centre, float s) {
 
 template <typename T, int EQ, int NC>
 __global__ void __launch_bounds__(256) k_features2d(const T* __restrict__ U, Grid2 G, long long plane,
-                                                    float* __restrict__ feat) {
+                                                    const Ctl* ctl, float* __restrict__ feat) {
+  const double t_bc = ctl->t;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < plane;
        c += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) k_features2d(const T* __restrict__ U, Gri
       const int fld = f * NC;  // density component of field group f
       const int ii = i + dx, jj = j + dy;
       if (ii >= 0 && ii < G.nx && jj >= 0 && jj < G.ny) return (float)U[fld * plane + (long long)jj * G.nx + ii];
-      return (float)load_ghost2<T, EQ, NC>(U, plane, G, fld, ii, jj);
+      return (float)load_ghost2<T, EQ, NC>(U, plane, G, fld, ii, jj, t_bc);
     };
     float centre;
     const float s = patch_scale(at, centre);
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(256) k_features2d(const T* __restrict__ U, Gri
 // ---------------------------------------------------------------------------
 template <typename T, int EQ, bool CHR, int D>
 __device__ __forceinline__ void pass_dev(const T* __restrict__ U, long long plane, const Grid2& G, int i, int j,
-                                         const WeightsT<T>& w, T g, T& dev) {
+                                         const WeightsT<T>& w, T g, double t_bc, T& dev) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   // frame offsets (n along the pass normal, t along the tangent)
   const int on[9] = {-1, 0, 1, -1, 0, 1, -1, 0, 1}, ot[9] = {-1, -1, -1, 0, 0, 0, 1, 1, 1};
@@ -86,7 +87,7 @@ __device__ __forceinline__ void pass_dev(const T* __restrict__ U, long long plan
   auto val = [&](int fld, int n, int t) -> T {
     const int ii = i + (D == 0 ? n : t), jj = j + (D == 0 ? t : n);
     if (ii >= 0 && ii < G.nx && jj >= 0 && jj < G.ny) return U[fld * plane + (long long)jj * G.nx + ii];
-    return load_ghost2<T, EQ, NC>(U, plane, G, fld, ii, jj);
+    return load_ghost2<T, EQ, NC>(U, plane, G, fld, ii, jj, t_bc);
   };
   T q[NC][17];
   for (int s = 0; s < 17; ++s) {
@@ -115,7 +116,9 @@ __device__ __forceinline__ void pass_dev(const T* __restrict__ U, long long plan
 
 template <typename T, int EQ, bool CHR>
 __global__ void __launch_bounds__(128) k_labels2d(const T* __restrict__ U, Grid2 G, long long plane,
-                                                  WeightParams wp, double gamma_gas, float* __restrict__ dev_out) {
+                                                  WeightParams wp, double gamma_gas, const Ctl* ctl,
+                                                  float* __restrict__ dev_out) {
+  const double t_bc = ctl->t;
   const WeightsT<T> wx = make_weights<T>(wp);
   WeightsT<T> wy = wx;
   wy.g[2] = wx.g[4];
@@ -124,8 +127,8 @@ __global__ void __launch_bounds__(128) k_labels2d(const T* __restrict__ U, Grid2
        c += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(c / G.nx), i = (int)(c - (long long)j * G.nx);
     T dev = T(0);
-    pass_dev<T, EQ, CHR, 0>(U, plane, G, i, j, wx, (T)gamma_gas, dev);
-    pass_dev<T, EQ, CHR, 1>(U, plane, G, i, j, wy, (T)gamma_gas, dev);
+    pass_dev<T, EQ, CHR, 0>(U, plane, G, i, j, wx, (T)gamma_gas, t_bc, dev);
+    pass_dev<T, EQ, CHR, 1>(U, plane, G, i, j, wy, (T)gamma_gas, t_bc, dev);
     dev_out[c] = (float)dev;
   }
 }
@@ -283,7 +286,8 @@ template <typename T, int EQ, int NC>
 __global__ void __launch_bounds__(256) k_mlp_infer2d(const T* __restrict__ U, Grid2 G, long long plane,
                                                      const __half* __restrict__ W1h, const __half* __restrict__ W2h,
                                                      const float* __restrict__ bias, float z_thresh,
-                                                     unsigned char* __restrict__ troubled) {
+                                                     const Ctl* ctl, unsigned char* __restrict__ troubled) {
+  const double t_bc = ctl->t;
   __shared__ float box[3][kBYH][kBXW];
   extern __shared__ __align__(16) unsigned char hw_dsm[];
   __half(*feat)[kFP] = reinterpret_cast<__half(*)[kFP]>(hw_dsm);  // [256][kFP], dynamic
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(256) k_mlp_infer2d(const T* __restrict__ U, Gr
       const int fld = f * NC;
       float v;
       if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = (float)U[fld * plane + (long long)j * G.nx + i];
-      else v = (float)load_ghost2<T, EQ, NC>(U, plane, G, fld, i, j);
+      else v = (float)load_ghost2<T, EQ, NC>(U, plane, G, fld, i, j, t_bc);
       box[f][r][cc] = v;
     }
     __syncthreads();
@@ -427,9 +431,9 @@ static unsigned grid_for(long long n, int threads, int num_sms, int per_sm) {
 }
 
 cudaError_t launch_features2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
-                              float* feat, int num_sms, cudaStream_t st) {
+                              const Ctl* ctl, float* feat, int num_sms, cudaStream_t st) {
   const unsigned b = grid_for(plane, 256, num_sms, 8);
-#define HW_F(T, EQ, NC) k_features2d<T, EQ, NC><<<b, 256, 0, st>>>(static_cast<const T*>(U), G, plane, feat)
+#define HW_F(T, EQ, NC) k_features2d<T, EQ, NC><<<b, 256, 0, st>>>(static_cast<const T*>(U), G, plane, ctl, feat)
   if (precision == HWENO_FP64) {
     if (equation == HWENO_EQ_EULER) HW_F(double, HWENO_EQ_EULER, 4);
     else if (equation == HWENO_EQ_BURGERS) HW_F(double, HWENO_EQ_BURGERS, 1);
@@ -444,11 +448,12 @@ cudaError_t launch_features2d(int precision, int equation, const void* U, const 
 }
 
 cudaError_t launch_labels2d(int precision, int equation, int charwise, const void* U, const Grid2& G,
-                            long long plane, const WeightParams& wp, double gamma_gas, float* dev, int num_sms,
-                            cudaStream_t st) {
+                            long long plane, const WeightParams& wp, double gamma_gas, const Ctl* ctl, float* dev,
+                            int num_sms, cudaStream_t st) {
   const unsigned b = grid_for(plane, 128, num_sms, 8);
   const bool chr = equation == HWENO_EQ_EULER && charwise;
-#define HW_L(T, EQ, C) k_labels2d<T, EQ, C><<<b, 128, 0, st>>>(static_cast<const T*>(U), G, plane, wp, gamma_gas, dev)
+#define HW_L(T, EQ, C) \
+  k_labels2d<T, EQ, C><<<b, 128, 0, st>>>(static_cast<const T*>(U), G, plane, wp, gamma_gas, ctl, dev)
   if (precision == HWENO_FP64) {
     if (equation == HWENO_EQ_EULER) { if (chr) HW_L(double, HWENO_EQ_EULER, true); else HW_L(double, HWENO_EQ_EULER, false); }
     else if (equation == HWENO_EQ_BURGERS) HW_L(double, HWENO_EQ_BURGERS, false);
@@ -499,12 +504,12 @@ cudaError_t prepare_mlp_infer2d() {
 }
 
 cudaError_t launch_mlp_infer2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
-                               const MlpDev& m, unsigned char* troubled, unsigned char* smooth, int num_sms,
-                               cudaStream_t st) {
+                               const MlpDev& m, const Ctl* ctl, unsigned char* troubled, unsigned char* smooth,
+                               int num_sms, cudaStream_t st) {
   const long long tiles = (long long)((G.nx + kTX - 1) / kTX) * ((G.ny + kTY - 1) / kTY);
   const unsigned b = (unsigned)(tiles < (long long)num_sms * 4 ? tiles : (long long)num_sms * 4);
 #define HW_I(T, EQ, NC) k_mlp_infer2d<T, EQ, NC><<<b, 256, kFeatBytes, st>>>(static_cast<const T*>(U), G, plane, \
-                                                                             m.W1h, m.W2h, m.bias, m.z_thresh, troubled)
+                                                                             m.W1h, m.W2h, m.bias, m.z_thresh, ctl, troubled)
   if (precision == HWENO_FP64) {
     if (equation == HWENO_EQ_EULER) HW_I(double, HWENO_EQ_EULER, 4);
     else if (equation == HWENO_EQ_BURGERS) HW_I(double, HWENO_EQ_BURGERS, 1);

@@ -98,10 +98,10 @@ cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long
                            double gamma_gas, double adv_x, double adv_y, Ctl* ctl, int num_sms,
                            cudaStream_t st);
 cudaError_t launch_features2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
-                              float* feat, int num_sms, cudaStream_t st);
+                              const Ctl* ctl, float* feat, int num_sms, cudaStream_t st);
 cudaError_t launch_labels2d(int precision, int equation, int charwise, const void* U, const Grid2& G,
-                            long long plane, const WeightParams& wp, double gamma_gas, float* dev, int num_sms,
-                            cudaStream_t st);
+                            long long plane, const WeightParams& wp, double gamma_gas, const Ctl* ctl, float* dev,
+                            int num_sms, cudaStream_t st);
 cudaError_t launch_mlp_train(const float* theta, const float* feat, const float* dev, const int* idx, int B,
                              float delta, float pos_weight, MlpWork& w, float* grad, cudaStream_t st);
 cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* g, float lr, int t, cudaStream_t st);
@@ -109,8 +109,8 @@ cudaError_t launch_mlp_predict(const float* theta, const float* feat, long long 
                                cudaStream_t st);
 cudaError_t prepare_mlp_infer2d();
 cudaError_t launch_mlp_infer2d(int precision, int equation, const void* U, const Grid2& G, long long plane,
-                               const MlpDev& m, unsigned char* troubled, unsigned char* smooth, int num_sms,
-                               cudaStream_t st);
+                               const MlpDev& m, const Ctl* ctl, unsigned char* troubled, unsigned char* smooth,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_ctl_begin(Ctl* ctl, int n, int dim, cudaStream_t st);
 cudaError_t launch_ctl_end(Ctl* ctl, int n, cudaStream_t st);
 cudaError_t launch_ctl_commit_alpha(Ctl* ctl, int n, cudaStream_t st);

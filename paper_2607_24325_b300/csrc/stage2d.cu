@@ -174,6 +174,8 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
   const Grid2& G = a.grid;
   const long long plane = a.plane;
   if (a.stage != 0 && a.ctl->done) return;
+  // time of the stage for time-dependent boundaries: t^n, t^n + dt, t^n + dt/2
+  const double t_bc = a.stage <= 1 ? a.ctl->t : a.ctl->t + (a.stage == 2 ? 1.0 : 0.5) * a.ctl->dt;
   const WeightsT<T> wx = make_weights<T>(a.wp);
   WeightsT<T> wy = wx;  // transposed frame: S2 <-> S4
   wy.g[2] = wx.g[4];
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
         const int i = min(max(i0 - 2 + cc, -2), G.nx + 1), j = min(max(j0 - 2 + rr, -2), G.ny + 1);
         T v;
         if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
-        else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j);
+        else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j, t_bc);
         box[f * kFS + rr * kBP + cc] = v;
       }
     }

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libhweno.so")
 HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL = 0, 1, 2, 3
 HWENO_ERR_TIMEOUT, HWENO_ERR_OOM, HWENO_ERR_STATE = 4, 5, 6
 EQ_ADVECTION, EQ_BURGERS, EQ_EULER = 0, 1, 2
-BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_OUTFLOW, BC_REFLECT, BC_INFLOW, BC_SPLIT, BC_SHOCK = 0, 1, 2, 3, 4, 5
 FP64, FP32, FP32_IND64 = 0, 1, 2
 DT_CFL, DT_CFL_DX53 = 0, 1
 BETA_MOMENT, BETA_TYPICAL = 0, 1
@@ -52,7 +52,7 @@ class hweno_config(C.Structure):
         ("lin_w", C.c_double * 5), ("eps", C.c_double), ("weight_pow", C.c_int),
         ("charwise", C.c_int), ("linear_weights", C.c_int), ("cfl", C.c_double), ("dt_rule", C.c_int),
         ("bc", C.c_int * 4), ("bc_state", (C.c_double * 4) * 4), ("precision", C.c_int),
-        ("smoothness", C.c_int),
+        ("smoothness", C.c_int), ("bc_state2", (C.c_double * 4) * 4), ("bc_param", (C.c_double * 2) * 4),
     ]
 
 
@@ -81,6 +81,8 @@ class Config:
     bc_state: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])
     precision: int = FP64
     smoothness: int = BETA_MOMENT
+    bc_state2: list = field(default_factory=lambda: [[0.0] * 4 for _ in range(4)])  # BC_SHOCK second state
+    bc_param: list = field(default_factory=lambda: [[0.0, 0.0] for _ in range(4)])  # BC_SPLIT / BC_SHOCK
 
     @property
     def ncomp(self) -> int:
@@ -105,6 +107,11 @@ class Config:
         c.eps, c.weight_pow, c.charwise, c.linear_weights = self.eps, self.weight_pow, self.charwise, self.linear_weights
         c.cfl, c.dt_rule, c.precision = self.cfl, self.dt_rule, self.precision
         c.smoothness = self.smoothness
+        for k in range(4):
+            for q in range(4):
+                c.bc_state2[k][q] = self.bc_state2[k][q]
+            for q in range(2):
+                c.bc_param[k][q] = self.bc_param[k][q]
         for k in range(4):
             c.bc[k] = self.bc[k]
             for q in range(4):

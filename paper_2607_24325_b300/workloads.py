@@ -312,3 +312,73 @@ def random_state(dim: int, shape, seed: int, euler: bool = False, gamma=GAMMA,
         nc = 4
     mom = moment_scale * rng.normal(size=(dim * nc,) + shape)
     return np.concatenate([ub, mom], axis=0)
+
+
+# --------------------------------------------------------------------------
+# Double Mach reflection (the paper's Sec. 3 example after Woodward and
+# Colella): a Mach 10 shock at 60 degrees to a reflecting wall on
+# [0, 4] x [0, 1]; the shock line x = 1/6 + y / sqrt(3) at t = 0 moves with
+# speed 10 along its normal, so it meets the top boundary at
+# x = 1/6 + (1 + 20 t) / sqrt(3).
+# --------------------------------------------------------------------------
+DMR_DOMAIN = (0.0, 4.0, 0.0, 1.0)
+DMR_X0 = 1.0 / 6.0
+_SQ3 = math.sqrt(3.0)
+
+
+def dmr_states(gamma=GAMMA):
+    """(post-shock, pre-shock) conservative states (rho, rho u, rho v, E)."""
+    post = prim_to_cons_2d(8.0, 8.25 * math.sin(math.pi / 3.0), -8.25 * math.cos(math.pi / 3.0), 116.5, gamma=gamma)
+    pre = prim_to_cons_2d(1.4, 0.0, 0.0, 1.0, gamma=gamma)
+    return np.asarray(post, dtype=np.float64), np.asarray(pre, dtype=np.float64)
+
+
+def dmr_boundary(gamma=GAMMA) -> dict:
+    """Boundary description of the example, as plain numbers shared by the
+    library config and the oracle problem: left inflow (post-shock), right
+    outflow, bottom split wall (post-shock for x < 1/6, reflective after),
+    top moving shock (post-shock behind x0 + s t, pre-shock ahead).  Codes:
+    1 outflow, 3 inflow, 4 split, 5 moving shock."""
+    post, pre = dmr_states(gamma)
+    z = [0.0] * 4
+    return {"bc": (3, 1, 4, 5),
+            "bc_state": [list(post), z, list(post), list(post)],
+            "bc_state2": [z, z, z, list(pre)],
+            "bc_param": [[0.0, 0.0], [0.0, 0.0], [DMR_X0, 0.0], [DMR_X0 + 1.0 / _SQ3, 20.0 / _SQ3]]}
+
+
+def _clip_int(z, h):
+    """Antiderivative of clip(z, 0, h) (zero at z <= 0)."""
+    z = np.asarray(z, dtype=np.float64)
+    return np.where(z <= 0.0, 0.0, np.where(z < h, 0.5 * z * z, 0.5 * h * h + h * (z - h)))
+
+
+def dmr_2d(nx, ny, gamma=GAMMA) -> np.ndarray:
+    """Exact cell averages and scaled moments of the initial state on the
+    example's domain: post-shock where x < 1/6 + y / sqrt(3).  The average
+    takes the exact area fraction left of the line; v-bar and w-bar are the
+    exact face-difference means (the jump times the share of the face-to-face
+    segment the line crosses)."""
+    post, pre = dmr_states(gamma)
+    xlo, xhi, ylo, yhi = DMR_DOMAIN
+    dx, dy = (xhi - xlo) / nx, (yhi - ylo) / ny
+    xl = (xlo + np.arange(nx) * dx)[None, :]
+    yb = (ylo + np.arange(ny) * dy)[:, None]
+    yt = yb + dy
+    b = 1.0 / _SQ3                        # x_s(y) = DMR_X0 + b y
+    z0 = DMR_X0 + b * yb - xl             # x_s - x_left at the cell's bottom and top
+    z1 = DMR_X0 + b * yt - xl
+    frac = (_clip_int(z1, dx) - _clip_int(z0, dx)) / (b * dx * dy)   # share with x < x_s(y)
+    frac = np.clip(frac, 0.0, 1.0)
+    ubar = post[:, None, None] * frac[None] + pre[:, None, None] * (1.0 - frac)[None]
+    # v-bar: y-share of the cell where the line lies between the two x faces
+    ylo_cross = (xl - DMR_X0) / b
+    yhi_cross = (xl + dx - DMR_X0) / b
+    sv = np.clip(np.minimum(yt, yhi_cross) - np.maximum(yb, ylo_cross), 0.0, None) / dy
+    vbar = (pre - post)[:, None, None] * sv[None]
+    # w-bar: x-share of the cell where the line lies between the two y faces
+    xs_b = DMR_X0 + b * yb
+    xs_t = DMR_X0 + b * yt
+    sw = np.clip(np.minimum(xl + dx, xs_t) - np.maximum(xl, xs_b), 0.0, None) / dx
+    wbar = (post - pre)[:, None, None] * sw[None]
+    return np.concatenate([ubar, vbar, wbar], axis=0)

@@ -15,7 +15,8 @@ def cfg_from(prob: oracle.Problem, precision: int = hw.FP64) -> hw.Config:
                      weight_pow=prob.weight_pow, charwise=prob.charwise,
                      linear_weights=prob.linear_weights, cfl=prob.cfl, dt_rule=prob.dt_rule,
                      bc=tuple(prob.bc), bc_state=[list(r) for r in prob.bc_state],
-                     precision=precision, smoothness=prob.smoothness)
+                     precision=precision, smoothness=prob.smoothness,
+                     bc_state2=[list(r) for r in prob.bc_state2], bc_param=[list(r) for r in prob.bc_param])
 
 
 def plane_rel_err(got, ref) -> float:
