@@ -59,6 +59,9 @@ BAD = [
     (dict(precision=5), "precision"),
     (dict(equation=hw.EQ_EULER, gamma_gas=1.0), "gamma_gas"),
     (dict(xhi=0.0), "domain"),
+    (dict(bc=(hw.BC_SPLIT, hw.BC_OUTFLOW, 0, 0)), "2D grid"),
+    (dict(bc=(hw.BC_OUTFLOW, 6, 0, 0)), "boundary"),
+    (dict(smoothness=2), "smoothness"),
 ]
 
 

@@ -178,6 +178,88 @@ def test_operator_typical_indicator_mixed(dim):
     assert ok, (e, tol)
 
 
+# ------------------- split wall and moving-shock boundaries (double Mach reflection)
+def _dmr_prob(nx, ny, t=0.0):
+    B = W.dmr_boundary()
+    return oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny, xlo=0.0, xhi=4.0, ylo=0.0, yhi=1.0,
+                          lin_w=W2D, bc=B["bc"], bc_state=B["bc_state"], bc_state2=B["bc_state2"],
+                          bc_param=B["bc_param"], t=t)
+
+
+def test_dmr_operator_fp64():
+    """One operator application on the double Mach reflection state at
+    t = 0.013 (the moving shock and the split wall in the ghost cells),
+    against the oracle: the bar of ill-conditioned shock data (R11)."""
+    nx, ny, t = 64, 16, 0.013
+    U = W.dmr_2d(nx, ny)
+    prob = _dmr_prob(nx, ny, t)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U)
+    hw.hweno_set_time(s.h, t)
+    L, D = s.apply_operator(12.0, 9.0)
+    L, D = L.cpu().numpy(), D.cpu().numpy()
+    s.close()
+    Lr, Dr, sL, sD = oracle_spread(prob, U, 12.0, 9.0)
+    ok, e, tol = within_spread(L, Lr, sL, TOL64)
+    assert ok, (e, tol)
+    ok, e, tol = within_spread(D, Dr, sD, TOL64)
+    assert ok, (e, tol)
+
+
+def test_split_and_shock_on_x_sides_fp64():
+    """The two time-dependent rules on the x sides (decided by the row's y),
+    rough data, at t = 0.2."""
+    nx, ny, t = 37, 45, 0.2
+    U = W.random_state(2, (ny, nx), seed=61, euler=True, moment_scale=0.3)
+    a = list(W.prim_to_cons_2d(1.3, 0.4, -0.2, 1.1))
+    b = list(W.prim_to_cons_2d(0.7, -0.1, 0.3, 0.6))
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny, xlo=0.0, xhi=1.0, ylo=-0.5, yhi=1.0,
+                          lin_w=W2D, bc=(oracle.BC_SPLIT, oracle.BC_SHOCK, oracle.BC_OUTFLOW, oracle.BC_REFLECT),
+                          bc_state=[a, a, a, a], bc_state2=[b, b, b, b],
+                          bc_param=[[0.3, 0.0], [-0.1, 2.0], [0.0, 0.0], [0.0, 0.0]], t=t)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(U)
+    hw.hweno_set_time(s.h, t)
+    L, D = s.apply_operator(2.2, 1.9)
+    L, D = L.cpu().numpy(), D.cpu().numpy()
+    s.close()
+    Lr, Dr = oracle.operator(prob, U, 2.2, 1.9)
+    assert plane_rel_err(L, Lr) < TOL64 and plane_rel_err(D, Dr) < TOL64
+
+
+@pytest.mark.parametrize("precision", [hw.FP64, hw.FP32_IND64])
+def test_dmr_short_run(precision):
+    """The double Mach reflection at 96 x 24 to t = 0.004 (the boundary
+    values follow the stage times): same steps and final time as the oracle;
+    relative L1 of every conserved component <= 1e-10 (FP64) / 2e-5 (FP32
+    stencil with FP64 indicators)."""
+    nx, ny, T = 96, 24, 0.004
+    U = W.dmr_2d(nx, ny)
+    prob = _dmr_prob(nx, ny)
+    s = hw.Solver(cfg_from(prob, precision))
+    s.set_state(U)
+    t, n = s.advance(T)
+    G = s.get_state(device=False).astype(np.float64)
+    s.close()
+    R, tr, nr = oracle.run(prob, U, T)
+    assert n == nr and abs(t - tr) < 1e-15
+    tol = 1e-10 if precision == hw.FP64 else 2e-5
+    for k in range(4):
+        assert np.abs(G[k] - R[k]).mean() / np.abs(R[k]).mean() < tol, k
+
+
+def test_step_advances_time():
+    nx, ny = 32, 8
+    prob = _dmr_prob(nx, ny)
+    s = hw.Solver(cfg_from(prob))
+    s.set_state(W.dmr_2d(nx, ny))
+    s.step(1e-4, 12.0, 9.0)
+    s.step(2e-4, 12.0, 9.0)
+    t, _ = hw.hweno_get_time(s.h)
+    s.close()
+    assert abs(t - 3e-4) < 1e-18
+
+
 # ------------------------------------------------------------ whole runs
 def test_run_1d_advection_config1():
     """1D advection sin(pi x) on [0,2], N = 160, CFL 0.6, to t = 2 (FP64)."""

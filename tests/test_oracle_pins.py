@@ -690,3 +690,92 @@ def test_typical_equals_moment_on_linear_data():
     b = oracle.recon_cell_2d(prob_t, q, 1.0, 1.0)
     np.testing.assert_allclose(a["beta"], b["beta"], rtol=1e-13, atol=1e-15)
     np.testing.assert_allclose(a["omega"], b["omega"], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Split wall and moving-shock boundaries (the double Mach reflection example,
+# Sec. 3): they reduce to the plain rules at their limits, and a moving shock
+# depends on x0 and t only through x0 + s t.
+# ---------------------------------------------------------------------------
+def _bc_problem(bc, st, st2=None, prm=None, t=0.0, eq=oracle.EQ_EULER):
+    z = [[0.0] * 4 for _ in range(4)]
+    return oracle.Problem(dim=2, equation=eq, nx=21, ny=13, xlo=0.0, xhi=2.1, ylo=0.0, yhi=1.3,
+                          lin_w=(0.6, 0.1, 0.1, 0.1, 0.1), bc=bc, bc_state=st, bc_state2=st2 or z,
+                          bc_param=prm or [[0.0, 0.0] for _ in range(4)], t=t)
+
+
+def _states():
+    a = list(W.prim_to_cons_2d(1.3, 0.4, -0.2, 1.1))
+    b = list(W.prim_to_cons_2d(0.7, -0.1, 0.3, 0.6))
+    return a, b
+
+
+def test_split_wall_limits():
+    U = W.random_state(2, (13, 21), seed=51, euler=True, moment_scale=0.3)
+    a, _ = _states()
+    st = [a, a, a, a]
+    for split, plain in ((10.0, oracle.BC_INFLOW), (-10.0, oracle.BC_REFLECT)):
+        prm = [[0.0, 0.0], [0.0, 0.0], [split, 0.0], [0.0, 0.0]]
+        p_s = _bc_problem((oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_SPLIT, oracle.BC_OUTFLOW), st, prm=prm)
+        p_p = _bc_problem((oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, plain, oracle.BC_OUTFLOW), st)
+        L1, D1 = oracle.operator(p_s, U, 2.0, 2.0)
+        L2, D2 = oracle.operator(p_p, U, 2.0, 2.0)
+        assert np.array_equal(L1, L2) and np.array_equal(D1, D2)
+    # a split inside the side differs from both
+    prm = [[0.0, 0.0], [0.0, 0.0], [1.05, 0.0], [0.0, 0.0]]
+    p_s = _bc_problem((oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_SPLIT, oracle.BC_OUTFLOW), st, prm=prm)
+    Ls, _ = oracle.operator(p_s, U, 2.0, 2.0)
+    Li, _ = oracle.operator(_bc_problem((1, 1, oracle.BC_INFLOW, 1), st), U, 2.0, 2.0)
+    Lr, _ = oracle.operator(_bc_problem((1, 1, oracle.BC_REFLECT, 1), st), U, 2.0, 2.0)
+    assert not np.array_equal(Ls, Li) and not np.array_equal(Ls, Lr)
+
+
+def test_moving_shock_limits_and_time_shift():
+    U = W.random_state(2, (13, 21), seed=52, euler=True, moment_scale=0.3)
+    a, b = _states()
+    st, st2 = [a, a, a, a], [b, b, b, b]
+    sides = (oracle.BC_SHOCK, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_SHOCK)
+    for x0, want in ((10.0, st), (-10.0, st2)):
+        prm = [[x0, 0.0], [0.0, 0.0], [0.0, 0.0], [x0, 0.0]]
+        L1, D1 = oracle.operator(_bc_problem(sides, st, st2, prm), U, 2.0, 2.0)
+        L2, D2 = oracle.operator(_bc_problem((oracle.BC_INFLOW, 1, 1, oracle.BC_INFLOW), want), U, 2.0, 2.0)
+        assert np.array_equal(L1, L2) and np.array_equal(D1, D2)
+    s, t, x0 = 3.0, 0.17, 0.2
+    moving = _bc_problem(sides, st, st2, [[x0, s], [0, 0], [0, 0], [x0, s]], t=t)
+    frozen = _bc_problem(sides, st, st2, [[x0 + s * t, 0.0], [0, 0], [0, 0], [x0 + s * t, 0.0]], t=0.0)
+    L1, D1 = oracle.operator(moving, U, 2.0, 2.0)
+    L2, D2 = oracle.operator(frozen, U, 2.0, 2.0)
+    np.testing.assert_allclose(L1, L2, rtol=0, atol=0)
+    np.testing.assert_allclose(D1, D2, rtol=0, atol=0)
+
+
+def test_moving_shock_step_uses_stage_times():
+    """A step from t0 with a moving shock equals the step from 0 with the
+    shock's position shifted by s t0 (the stage times are t0 + {0, dt, dt/2})."""
+    U0 = W.random_state(2, (13, 21), seed=53, euler=True, moment_scale=0.2)
+    a, b = _states()
+    st, st2 = [a, a, a, a], [b, b, b, b]
+    sides = (oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_SHOCK)
+    s, t0, x0 = 5.0, 0.05, 0.3
+    U1 = oracle.step(_bc_problem(sides, st, st2, [[0, 0], [0, 0], [0, 0], [x0, s]], t=t0), U0, 0.01, 4.0, 4.0)
+    U2 = oracle.step(_bc_problem(sides, st, st2, [[0, 0], [0, 0], [0, 0], [x0 + s * t0, s]], t=0.0), U0, 0.01,
+                     4.0, 4.0)
+    np.testing.assert_allclose(U1, U2, rtol=0, atol=1e-15)
+    # and the boundary does move within the step: a frozen shock gives another result
+    U3 = oracle.step(_bc_problem(sides, st, st2, [[0, 0], [0, 0], [0, 0], [x0 + s * t0, 0.0]], t=0.0), U0, 0.01,
+                     4.0, 4.0)
+    assert np.abs(U3 - U1).max() > 1e-6
+
+
+def test_dmr_initial_state_matches_fine_sampling():
+    """The double Mach reflection initial averages against a fine sampling
+    of the oblique shock (sampling error ~ 1/k^2 on cut cells)."""
+    nx, ny, k = 16, 4, 512
+    U = W.dmr_2d(nx, ny)
+    post, pre = W.dmr_states()
+    dx, dy = 4.0 / nx, 1.0 / ny
+    xs = (np.arange(nx * k) + 0.5) * dx / k
+    ys = (np.arange(ny * k) + 0.5) * dy / k
+    X, Y = np.meshgrid(xs, ys)
+    fr = (X < 1.0 / 6.0 + Y / math.sqrt(3.0)).astype(float).reshape(ny, k, nx, k).mean(axis=(1, 3))
+    assert np.abs(post[0] * fr + pre[0] * (1 - fr) - U[0]).max() < 1e-4
