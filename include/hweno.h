@@ -232,14 +232,21 @@ hweno_status hweno_selftest_convert(const float* f_in, double* wide_out, const d
  * blocks per SM, persistent).  Allocates and frees two temporary buffers. */
 hweno_status hweno_autotune(hweno_solver* s, int reps, double* best_ms, int* shape_out);
 
-/* ---- Batches of independent 1D problems of uneven sizes (one launch per
- * stage for all instances, per-instance alpha, dt, time and done flag). ---- */
-/* cfgs[n] are 1D configs with the same equation, precision and weights. */
+/* ---- Batches of independent problems of uneven sizes, all 1D or all 2D
+ * (one launch per stage for all instances: 1D a table of 30-cell warp tasks,
+ * 2D a table of 30 x 30 tiles; per-instance alpha, dt, time and done flag;
+ * whole steps replayed from a CUDA graph). ---- */
+/* cfgs[n] share dim, equation, precision, characteristic/component-wise
+ * reconstruction, linear weights, eps, weight power, indicator form, gamma
+ * and the advection velocity; grid sizes, domains, boundaries, CFL numbers
+ * and dt rules are per instance.  The learned indicator serves single
+ * solvers only. */
 hweno_status hweno_batch_create(int n, const hweno_config* cfgs, void* cuda_stream,
                                 hweno_batch** out);
 void hweno_batch_destroy(hweno_batch* b);
 void* hweno_batch_stream(hweno_batch* b);
-/* Total cells (sum of nx) and per-instance offsets (n+1 entries, host). */
+/* Total cells (sum of nx, or of nx * ny in 2D) and per-instance offsets
+ * (n+1 entries, host). */
 hweno_status hweno_batch_layout(const hweno_batch* b, size_t* total_cells, size_t* offsets);
 /* U is [nf][total_cells]: instance k owns cells offsets[k] .. offsets[k+1]-1
  * of every field plane. */
@@ -252,8 +259,10 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
                                  double* t_out, int* steps_out);
 /* The autotuner of hweno_autotune for a batch (all instances at once). */
 hweno_status hweno_batch_autotune(hweno_batch* b, int reps, double* best_ms, int* shape_out);
-/* Apply the operator to every instance with per-instance alpha (host array):
- * L_out [nf][total], dhat_out [nc][total] (device buffers). */
+/* Apply the operator to every instance with per-instance Lax-Friedrichs
+ * constants (host array): alpha[n] for 1D, alpha[n][2] = (alpha_x, alpha_y)
+ * for 2D; L_out [nf][total], dhat_out [nc*dim][total] (device buffers; a 2D
+ * instance occupies [offsets[k], offsets[k+1]) of every plane, row-major). */
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,
                                         void* dhat_out);
 

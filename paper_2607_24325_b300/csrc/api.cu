@@ -51,7 +51,7 @@ constexpr int kGraphSteps = 16;
 hweno_status validate(const hweno_config* c, int expect_dim) {
   if (!c) return fail(HWENO_ERR_ARG, "config is NULL");
   if (c->dim != 1 && c->dim != 2) return fail(HWENO_ERR_ARG, "dim must be 1 or 2 (got %d)", c->dim);
-  if (expect_dim && c->dim != expect_dim) return fail(HWENO_ERR_ARG, "batches hold 1D problems only");
+  if (expect_dim && c->dim != expect_dim) return fail(HWENO_ERR_ARG, "all configs of a batch need the same dim");
   if (c->nx < 3 || (c->dim == 2 && c->ny < 3))
     return fail(HWENO_ERR_ARG, "need at least 3 cells per direction (nx=%d ny=%d)", c->nx, c->ny);
   if ((long long)c->nx * (c->dim == 2 ? c->ny : 1) > (1LL << 31))
@@ -88,6 +88,27 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
   return HWENO_OK;
 }
 
+// The 2D grid descriptor of a configuration.
+hw::Grid2 grid_of(const hweno_config& c) {
+  hw::Grid2 g{};
+  g.nx = c.nx;
+  g.ny = c.ny;
+  for (int q = 0; q < 4; ++q) {
+    g.bc[q] = c.bc[q];
+    for (int r = 0; r < 4; ++r) {
+      g.st[q][r] = c.bc_state[q][r];
+      g.st2[q][r] = c.bc_state2[q][r];
+    }
+    g.bcp[q][0] = c.bc_param[q][0];
+    g.bcp[q][1] = c.bc_param[q][1];
+  }
+  g.dx = (c.xhi - c.xlo) / c.nx;
+  g.dy = (c.yhi - c.ylo) / c.ny;
+  g.xlo = c.xlo;
+  g.ylo = c.ylo;
+  return g;
+}
+
 }  // namespace
 
 namespace hw {
@@ -117,8 +138,14 @@ struct Engine {
   std::vector<long long> offsets;
   int2* tasks_d = nullptr;
   int ntasks = 0;
-  double* alpha_op = nullptr;    // device [n_inst]
+  double* alpha_op = nullptr;    // device [n_inst] (1D) or [n_inst][2] (2D batch)
   hw::Grid2 grid{};
+  // 2D batch: per-instance descriptors and the tile table over all instances
+  bool batch2 = false;
+  std::vector<hw::Inst2> inst2_h;
+  hw::Inst2* inst2_d = nullptr;
+  hw::Tile2* tiles2_d = nullptr;
+  long long ntiles2 = 0;
   hw::WeightParams wp{};
   cudaGraphExec_t gexec = nullptr;
   bool has_state = false;
@@ -142,14 +169,16 @@ struct Engine {
     if (gexec) cudaGraphExecDestroy(gexec);
     cudaFree(S); cudaFree(A); cudaFree(B); cudaFree(H);
     cudaFree(ctl); cudaFree(ctl_manual); cudaFree(inst_d); cudaFree(tasks_d); cudaFree(alpha_op);
+    cudaFree(inst2_d); cudaFree(tiles2_d);
     cudaFree(mlp_w); cudaFree(mlp_bias); cudaFree(troubled); cudaFree(smooth);
     if (ctl_host) cudaFreeHost(ctl_host);
     if (ev) cudaEventDestroy(ev);
     if (own) cudaStreamDestroy(own);
   }
 
-  hweno_status init(int n, const hweno_config* cfgs, void* stream) {
+  hweno_status init(int n, const hweno_config* cfgs, void* stream, bool batch = false) {
     cfg = cfgs[0];
+    batch2 = batch && cfg.dim == 2;
     dim = cfg.dim;
     nc = cfg.equation == HWENO_EQ_EULER ? (dim == 1 ? 3 : 4) : 1;
     nf = nc * (dim + 1);
@@ -178,7 +207,7 @@ struct Engine {
         I.n = c.nx;
         I.bc_lo = c.bc[0];
         I.bc_hi = c.bc[1];
-        I.dx = (c.xhi - c.xlo) / c.nx;
+        hw::set_spacing(I, c.xlo, c.xhi, c.nx);
         for (int q = 0; q < 4; ++q) { I.st_lo[q] = c.bc_state[0][q]; I.st_hi[q] = c.bc_state[1][q]; }
         offsets[k] = off;
         for (int s = 0; s < c.nx; s += hw::kTile1) tasks.push_back(make_int2(k, s));
@@ -197,22 +226,44 @@ struct Engine {
       HW_CK(cudaMemcpy(inst_d, inst_h.data(), sizeof(hw::Inst1) * n, cudaMemcpyHostToDevice));
       HW_CK(cudaMalloc(&tasks_d, sizeof(int2) * tasks.size()));
       HW_CK(cudaMemcpy(tasks_d, tasks.data(), sizeof(int2) * tasks.size(), cudaMemcpyHostToDevice));
-    } else {
-      grid.nx = cfg.nx;
-      grid.ny = cfg.ny;
-      for (int q = 0; q < 4; ++q) {
-        grid.bc[q] = cfg.bc[q];
-        for (int r = 0; r < 4; ++r) {
-          grid.st[q][r] = cfg.bc_state[q][r];
-          grid.st2[q][r] = cfg.bc_state2[q][r];
-        }
-        grid.bcp[q][0] = cfg.bc_param[q][0];
-        grid.bcp[q][1] = cfg.bc_param[q][1];
+    } else if (batch2) {
+      inst2_h.resize(n);
+      offsets.resize(n + 1);
+      std::vector<hw::Tile2> tiles;
+      long long off = 0;
+      for (int k = 0; k < n; ++k) {
+        const hweno_config& c = cfgs[k];
+        hw::Inst2& I = inst2_h[k];
+        I.off = off;
+        I.grid = grid_of(c);
+        I.idx = 1.0 / I.grid.dx;
+        I.idy = 1.0 / I.grid.dy;
+        I.dyx = I.grid.dy / I.grid.dx;
+        I.dxy = I.grid.dx / I.grid.dy;
+        I.idxf = (float)I.idx; I.idyf = (float)I.idy; I.dyxf = (float)I.dyx; I.dxyf = (float)I.dxy;
+        offsets[k] = off;
+        for (int j0 = 0; j0 < c.ny; j0 += hw::kTile2)
+          for (int i0 = 0; i0 < c.nx; i0 += hw::kTile2) tiles.push_back(hw::Tile2{k, i0, j0, 0});
+        off += (long long)c.nx * c.ny;
+        hw::Ctl& C = ctl_init[k];
+        std::memset(&C, 0, sizeof C);
+        const bool r53 = c.dt_rule == HWENO_DT_CFL_DX53;
+        C.hx = r53 ? std::pow(I.grid.dx, 5.0 / 3.0) : I.grid.dx;
+        C.hy = r53 ? std::pow(I.grid.dy, 5.0 / 3.0) : I.grid.dy;
+        C.cfl = c.cfl;
+        C.done = 1;
       }
-      grid.dx = (cfg.xhi - cfg.xlo) / cfg.nx;
-      grid.dy = (cfg.yhi - cfg.ylo) / cfg.ny;
-      grid.xlo = cfg.xlo;
-      grid.ylo = cfg.ylo;
+      offsets[n] = off;
+      cells = off;
+      grid = inst2_h[0].grid;
+      ntiles2 = (long long)tiles.size();
+      HW_CK(cudaMalloc(&inst2_d, sizeof(hw::Inst2) * n));
+      HW_CK(cudaMemcpy(inst2_d, inst2_h.data(), sizeof(hw::Inst2) * n, cudaMemcpyHostToDevice));
+      HW_CK(cudaMalloc(&tiles2_d, sizeof(hw::Tile2) * tiles.size()));
+      HW_CK(cudaMemcpy(tiles2_d, tiles.data(), sizeof(hw::Tile2) * tiles.size(), cudaMemcpyHostToDevice));
+      HW_CK(hw::prepare_stage2d(prec, cfg.equation, cfg.charwise, wp, true));
+    } else {
+      grid = grid_of(cfg);
       cells = (long long)cfg.nx * cfg.ny;
       offsets = {0, cells};
       hw::Ctl& C = ctl_init[0];
@@ -222,7 +273,7 @@ struct Engine {
       C.hy = r53 ? std::pow(grid.dy, 5.0 / 3.0) : grid.dy;
       C.cfl = cfg.cfl;
       C.done = 1;
-      HW_CK(hw::prepare_stage2d(prec, cfg.equation, cfg.charwise));
+      HW_CK(hw::prepare_stage2d(prec, cfg.equation, cfg.charwise, wp, false));
     }
     const size_t plane = (size_t)cells * esz;
     HW_CK(cudaMalloc(&S, plane * nf));
@@ -231,7 +282,7 @@ struct Engine {
     HW_CK(cudaMalloc(&H, plane * nd));
     HW_CK(cudaMalloc(&ctl, sizeof(hw::Ctl) * n));
     HW_CK(cudaMalloc(&ctl_manual, sizeof(hw::Ctl) * n));
-    HW_CK(cudaMalloc(&alpha_op, sizeof(double) * n));
+    HW_CK(cudaMalloc(&alpha_op, sizeof(double) * 2 * n));
     HW_CK(cudaMallocHost(&ctl_host, sizeof(hw::Ctl) * n));
     HW_CK(cudaMemcpy(ctl, ctl_init.data(), sizeof(hw::Ctl) * n, cudaMemcpyHostToDevice));
     HW_CK(cudaMemcpy(ctl_manual, ctl_init.data(), sizeof(hw::Ctl) * n, cudaMemcpyHostToDevice));
@@ -258,6 +309,7 @@ struct Engine {
       a.inst = inst_d; a.tasks = tasks_d; a.ntasks = ntasks; a.total = cells;
       a.ctl = c; a.alpha_op = alpha_op; a.stage = s;
       a.gamma_gas = cfg.gamma_gas; a.adv = cfg.adv_x; a.wp = wp;
+      a.gammaf = (float)cfg.gamma_gas; a.advf = (float)cfg.adv_x;
       HW_CK(hw::launch_stage1d(prec, cfg.equation, cfg.charwise, a, num_sms, own, shape));
     } else {
       hw::Stage2Args a{};
@@ -267,6 +319,13 @@ struct Engine {
       a.f32 = hw::stage2_f32(grid, ax, ay, cfg.gamma_gas, cfg.adv_x, cfg.adv_y);
       a.plane = cells;
       a.smooth = learned && s > 0 ? smooth : nullptr;
+      if (batch2) {
+        a.batched = 1;
+        a.inst = inst2_d;
+        a.tiles = tiles2_d;
+        a.ntiles = ntiles2;
+        a.alpha_op = alpha_op;
+      }
       HW_CK(hw::launch_stage2d(prec, cfg.equation, cfg.charwise, a, num_sms, own, shape));
     }
     return HWENO_OK;
@@ -333,8 +392,13 @@ struct Engine {
     if (dim == 1)
       HW_CK(hw::launch_alpha1d(prec, cfg.equation, S, cells, inst_d, tasks_d, ntasks, cfg.gamma_gas,
                                cfg.adv_x, ctl, num_sms, own));
+    else if (batch2)
+      for (int k = 0; k < n_inst; ++k)
+        HW_CK(hw::launch_alpha2d(prec, cfg.equation, static_cast<const char*>(S) + offsets[k] * esz,
+                                 offsets[k + 1] - offsets[k], cells, cfg.gamma_gas, cfg.adv_x, cfg.adv_y,
+                                 ctl + k, num_sms, own));
     else
-      HW_CK(hw::launch_alpha2d(prec, cfg.equation, S, cells, cfg.gamma_gas, cfg.adv_x, cfg.adv_y, ctl,
+      HW_CK(hw::launch_alpha2d(prec, cfg.equation, S, cells, cells, cfg.gamma_gas, cfg.adv_x, cfg.adv_y, ctl,
                                num_sms, own));
     HW_CK(hw::launch_ctl_commit_alpha(ctl, n_inst, own));
     return HWENO_OK;
@@ -466,16 +530,16 @@ struct Engine {
     if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
     if (!L || !dh) return fail(HWENO_ERR_ARG, "output pointer is NULL");
     HW_TRY(enter());
-    if (dim == 1) {
+    if (dim == 1 || batch2) {
       HW_CK(cudaStreamSynchronize(own));
-      HW_CK(cudaMemcpy(alpha_op, ax, sizeof(double) * n_inst, cudaMemcpyHostToDevice));
+      HW_CK(cudaMemcpy(alpha_op, ax, sizeof(double) * n_inst * (batch2 ? 2 : 1), cudaMemcpyHostToDevice));
     }
     HW_TRY(stage(0, S, L, ctl, ax[0], ay, dh));
     return leave();
   }
 
   hweno_status load_indicator(const float* theta, int n, double p_threshold) {
-    if (dim != 2) return fail(HWENO_ERR_ARG, "the learned indicator serves 2D solvers");
+    if (dim != 2 || batch2) return fail(HWENO_ERR_ARG, "the learned indicator serves single 2D solvers");
     if (!theta || n != hw::kMlpParams) return fail(HWENO_ERR_ARG, "expected %d network parameters", hw::kMlpParams);
     if (!(p_threshold > 0.0 && p_threshold < 1.0)) return fail(HWENO_ERR_ARG, "threshold must lie in (0, 1)");
     for (int k = 0; k < n; ++k)
@@ -536,8 +600,8 @@ struct Engine {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     HW_CK(cudaEventCreate(&e0));
     HW_CK(cudaEventCreate(&e1));
-    std::vector<double> a0(n_inst, 1.0);
-    if (dim == 1) HW_CK(cudaMemcpy(alpha_op, a0.data(), sizeof(double) * n_inst, cudaMemcpyHostToDevice));
+    std::vector<double> a0(2 * n_inst, 1.0);
+    if (dim == 1 || batch2) HW_CK(cudaMemcpy(alpha_op, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice));
     const hw::LaunchShape keep = shape;
     double best = 1e300;
     hw::LaunchShape pick = keep;
@@ -698,18 +762,18 @@ hweno_status hweno_batch_create(int n, const hweno_config* cfgs, void* cuda_stre
   *out = nullptr;
   if (n < 1 || !cfgs) return fail(HWENO_ERR_ARG, "need at least one config");
   for (int k = 0; k < n; ++k) {
-    HW_TRY(validate(&cfgs[k], 1));
+    HW_TRY(validate(&cfgs[k], cfgs[0].dim));
     const hweno_config &a = cfgs[0], &b = cfgs[k];
     bool same = a.equation == b.equation && a.precision == b.precision && a.charwise == b.charwise &&
                 a.linear_weights == b.linear_weights && a.weight_pow == b.weight_pow && a.eps == b.eps &&
                 a.smoothness == b.smoothness &&
-                a.gamma_gas == b.gamma_gas && a.adv_x == b.adv_x;
-    for (int m = 0; m < 3; ++m) same = same && a.lin_w[m] == b.lin_w[m];
+                a.gamma_gas == b.gamma_gas && a.adv_x == b.adv_x && (a.dim == 1 || a.adv_y == b.adv_y);
+    for (int m = 0; m < (a.dim == 1 ? 3 : 5); ++m) same = same && a.lin_w[m] == b.lin_w[m];
     if (!same) return fail(HWENO_ERR_ARG, "config %d differs from config 0 in a batch-wide parameter", k);
   }
   hweno_batch* b = new (std::nothrow) hweno_batch();
   if (!b) return fail(HWENO_ERR_OOM, "host allocation failed");
-  hweno_status st = b->e.init(n, cfgs, cuda_stream);
+  hweno_status st = b->e.init(n, cfgs, cuda_stream, true);
   if (st != HWENO_OK) {
     delete b;
     return st;
@@ -753,7 +817,7 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,
                                         void* dhat_out) {
   if (!b || !alpha) return fail(HWENO_ERR_ARG, "batch or alpha is NULL");
-  for (int k = 0; k < b->e.n_inst; ++k)
+  for (int k = 0; k < b->e.n_inst * b->e.dim; ++k)
     if (!(alpha[k] >= 0.0)) return fail(HWENO_ERR_ARG, "alpha must be >= 0");
   return b->e.apply_operator(alpha, 0.0, L_out, dhat_out);
 }

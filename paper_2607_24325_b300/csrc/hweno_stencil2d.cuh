@@ -49,21 +49,32 @@ __device__ constexpr int frame_field(int d, int k) {
 }
 
 // The rule a side applies to one ghost cell: split walls and moving shocks
-// resolve, by the coordinate `along` of the ghost cell's centre along the
-// side and the stage time t, into an inflow state or a mirror.
+// resolve, by the coordinate of the ghost cell's centre along the side
+// (lo + (idx + 1/2) h) and the stage time t, into an inflow state or a
+// mirror.  The coordinate is formed only for those two kinds of side.
 struct SideRule {
   int bc;
   const double* st;
 };
-__device__ __forceinline__ SideRule side_rule(const Grid2& G, int sd, double along, double t) {
+__device__ __forceinline__ SideRule side_rule(const Grid2& G, int sd, double lo, int idx, double h, double t) {
   SideRule r{G.bc[sd], G.st[sd]};
-  if (r.bc == HWENO_BC_SPLIT) {
-    r.bc = along < G.bcp[sd][0] ? HWENO_BC_INFLOW : HWENO_BC_REFLECT;
-  } else if (r.bc == HWENO_BC_SHOCK) {
-    r.bc = HWENO_BC_INFLOW;
-    if (!(along < G.bcp[sd][0] + G.bcp[sd][1] * t)) r.st = G.st2[sd];
+  if (r.bc == HWENO_BC_SPLIT || r.bc == HWENO_BC_SHOCK) {
+    const double along = lo + (idx + 0.5) * h;
+    if (r.bc == HWENO_BC_SPLIT) {
+      r.bc = along < G.bcp[sd][0] ? HWENO_BC_INFLOW : HWENO_BC_REFLECT;
+    } else {
+      r.bc = HWENO_BC_INFLOW;
+      if (!(along < G.bcp[sd][0] + G.bcp[sd][1] * t)) r.st = G.st2[sd];
+    }
   }
   return r;
+}
+
+// frame_field with the direction known only at run time (the compiler folds
+// the component and field constants; D selects between two of them).
+template <int EQ, int NC>
+__device__ __forceinline__ int frame_field_rt(int D, int d, int k) {
+  return D == 0 ? frame_field<0, EQ, NC>(d, k) : frame_field<1, EQ, NC>(d, k);
 }
 
 // Value of field f at cell (i, j), ghost cells resolved as "x sides for the
@@ -73,12 +84,11 @@ template <typename T, int EQ, int NC>
 __device__ __forceinline__ T load_ghost2(const T* __restrict__ in, long long plane, const Grid2& G,
                                          int f, int i, int j, double t) {
   const int d = f / NC, k = f % NC;
-  const double xc = G.xlo + (i + 0.5) * G.dx;   // the column's centre (y sides)
-  const SideRule ry0 = side_rule(G, 2, xc, t), ry1 = side_rule(G, 3, xc, t);
+  // y sides decide by the column's centre x, x sides by the source row's centre y
+  const SideRule ry0 = side_rule(G, 2, G.xlo, i, G.dx, t), ry1 = side_rule(G, 3, G.xlo, i, G.dx, t);
   const GhostMap gy = ghost_map(j, G.ny, ry0.bc, ry1.bc);
   if (gy.fixed) return d == 0 ? (T)(gy.side ? ry1.st : ry0.st)[k] : T(0);
-  const double yc = G.ylo + (gy.src + 0.5) * G.dy;  // the source row's centre (x sides)
-  const SideRule rx0 = side_rule(G, 0, yc, t), rx1 = side_rule(G, 1, yc, t);
+  const SideRule rx0 = side_rule(G, 0, G.ylo, gy.src, G.dy, t), rx1 = side_rule(G, 1, G.ylo, gy.src, G.dy, t);
   const GhostMap gx = ghost_map(i, G.nx, rx0.bc, rx1.bc);
   T v;
   if (gx.fixed) {

@@ -59,8 +59,18 @@ struct Inst1 {
   int bc_lo, bc_hi;    // HWENO_BC_*
   int pad;
   double dx;
+  double idx;                 // 1 / dx
+  float dxf, idxf;            // the same in FP32 (host-rounded, for the FP32 kernels)
   double st_lo[4], st_hi[4];  // inflow states (conservative)
 };
+
+// Grid spacing fields of an instance from its cell count and extent.
+inline void set_spacing(Inst1& I, double xlo, double xhi, int nx) {
+  I.dx = (xhi - xlo) / nx;
+  I.idx = 1.0 / I.dx;
+  I.dxf = (float)I.dx;
+  I.idxf = (float)I.idx;
+}
 
 // 2D grid description.
 struct Grid2 {
@@ -71,6 +81,19 @@ struct Grid2 {
   double st[4][4];
   double st2[4][4];   // second state of HWENO_BC_SHOCK sides
   double bcp[4][2];   // HWENO_BC_SPLIT / HWENO_BC_SHOCK parameters
+};
+
+// One 2D instance inside the concatenated field planes of a 2D batch.
+struct Inst2 {
+  long long off;                   // first cell of the instance in every field plane
+  Grid2 grid;
+  double idx, idy, dyx, dxy;       // 1/dx, 1/dy, dy/dx, dx/dy
+  float idxf, idyf, dyxf, dxyf;    // the same rounded to FP32
+};
+
+// One 30 x 30 tile of a 2D batch: its instance and its origin.
+struct Tile2 {
+  int inst, i0, j0, pad;
 };
 
 }  // namespace hw

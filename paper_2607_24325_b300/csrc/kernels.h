@@ -25,6 +25,7 @@ struct Stage1Args {
   const double* alpha_op; // stage 0: per-instance alpha
   int stage;
   double gamma_gas, adv;
+  float gammaf, advf;     // the same, host-rounded to FP32
   WeightParams wp;
 };
 
@@ -58,8 +59,16 @@ struct Stage2Args {
   double gamma_gas, adv_x, adv_y;
   WeightParams wp;
   Stage2F32 f32;
-  long long plane;        // nx * ny
+  long long plane;        // field plane stride: nx * ny, or the total cells of a batch
   const unsigned char* smooth;  // learned indicator: 1 = linear path allowed (nullptr: off)
+  // 2D batch (batched = 1): per-instance descriptors, the tile table and,
+  // for stage 0, per-instance (alpha_x, alpha_y); ctl holds one block per
+  // instance.  grid, ax_op, ay_op and f32's grid ratios are then unused.
+  int batched;
+  const Inst2* inst;
+  const Tile2* tiles;
+  long long ntiles;
+  const double* alpha_op;
 };
 
 // Learned troubled-cell indicator: per-sample training buffers and the
@@ -76,6 +85,7 @@ struct MlpDev {
 constexpr int kMlpParams = 3521;
 
 constexpr int kTile1 = 30;   // interior cells per warp task (32 lanes - 2 ring cells)
+constexpr int kTile2 = 30;   // interior cells per 2D tile edge (the stage kernel's tile)
 
 // Launch shapes chosen by the autotuner: 1D warps per block (1..8) and a cap
 // on resident blocks per SM for the persistent grid; 2D persistent grid
@@ -93,8 +103,8 @@ cudaError_t launch_alpha1d(int precision, int equation, const void* U, long long
                            double adv, Ctl* ctl, int num_sms, cudaStream_t st);
 cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a,
                            int num_sms, cudaStream_t st, const LaunchShape& shape = LaunchShape());
-cudaError_t prepare_stage2d(int precision, int equation, int charwise);
-cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane,
+cudaError_t prepare_stage2d(int precision, int equation, int charwise, const WeightParams& wp, bool batched);
+cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long count, long long plane,
                            double gamma_gas, double adv_x, double adv_y, Ctl* ctl, int num_sms,
                            cudaStream_t st);
 cudaError_t launch_features2d(int precision, int equation, const void* U, const Grid2& G, long long plane,

@@ -123,7 +123,7 @@ extern "C" hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const voi
   inst.n = cfg->nx;
   inst.bc_lo = cfg->bc[0];
   inst.bc_hi = cfg->bc[1];
-  inst.dx = (cfg->xhi - cfg->xlo) / cfg->nx;
+  hw::set_spacing(inst, cfg->xlo, cfg->xhi, cfg->nx);
   for (int q = 0; q < 4; ++q) {
     inst.st_lo[q] = cfg->bc_state[0][q];
     inst.st_hi[q] = cfg->bc_state[1][q];
@@ -131,6 +131,8 @@ extern "C" hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const voi
   hw::Ctl ctl{};
   ctl.dt = dt;
   ctl.ax = alpha;
+  ctl.dtf = (float)dt;
+  ctl.axf = (float)alpha;
   ctl.hx = inst.dx;
   ctl.hy = 1.0;
   ctl.cfl = cfg->cfl;

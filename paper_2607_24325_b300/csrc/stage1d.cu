@@ -77,7 +77,10 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
   T* __restrict__ hat = static_cast<T*>(a.hat);
   const WeightsT<T> w = make_weights<T>(a.wp);
   const WeightsT<double> w64 = make_weights<double>(a.wp);
-  const T g = (T)a.gamma_gas, adv = (T)a.adv;
+  // FP32 kernels take host-rounded FP32 scalars (a conversion re-done at
+  // each use would issue on the FP64 pipe)
+  const T g = sizeof(T) == 4 ? (T)a.gammaf : (T)a.gamma_gas;
+  const T adv = sizeof(T) == 4 ? (T)a.advf : (T)a.adv;
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const long long total = a.total;
@@ -85,14 +88,19 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
   for (int task = blockIdx.x * wpb + (threadIdx.x >> 5); task < a.ntasks; task += gridDim.x * wpb) {
     const int2 tk = a.tasks[task];
     const Inst1 I = a.inst[tk.x];
-    double dt = 0.0, alpha;
+    T tdt = T(0), alpha;
     if (a.stage == 0) {
-      alpha = a.alpha_op[tk.x];
+      alpha = (T)a.alpha_op[tk.x];
     } else {
       const Ctl* c = a.ctl + tk.x;
       if (c->done) continue;  // warp-uniform
-      dt = c->dt;
-      alpha = c->ax;
+      if constexpr (sizeof(T) == 4) {
+        tdt = c->dtf;
+        alpha = c->axf;
+      } else {
+        tdt = c->dt;
+        alpha = c->ax;
+      }
     }
     const int cell = tk.y - 1 + lane;
     const int lc = min(cell, I.n + 1);
@@ -108,7 +116,14 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
     if (lane == 0) load_cell1<T, NC, EQ>(in, total, I, lc - 1, um, vm);
     if (lane == 31) load_cell1<T, NC, EQ>(in, total, I, min(cell + 1, I.n + 1), up, vp);
 
-    const T dx = (T)I.dx, idx = (T)(1.0 / I.dx);
+    T dx, idx;
+    if constexpr (sizeof(T) == 4) {
+      dx = I.dxf;
+      idx = I.idxf;
+    } else {
+      dx = I.dx;
+      idx = I.idx;
+    }
     T uL[NC], uR[NC], dL[NC], dR[NC], vh[NC];
     if constexpr (CHR) {
       const Eig<T> e = eig1<T>(ub[0], ub[1], ub[2], g);
@@ -137,7 +152,7 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
       Um[k] = __shfl_up_sync(HW_FULL_MASK, uR[k], 1);
       Vm[k] = __shfl_up_sync(HW_FULL_MASK, dR[k], 1);
     }
-    lf_flux1<T, NC, EQ>(Um, uL, Vm, dL, (T)alpha, g, adv, Fu, Fv);
+    lf_flux1<T, NC, EQ>(Um, uL, Vm, dL, alpha, g, adv, Fu, Fv);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
@@ -147,7 +162,6 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
     double rad = 0.0;
     if (interior) {
       const long long p = I.off + cell;
-      const T tdt = (T)dt;
       T nu[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {

@@ -24,6 +24,8 @@
 
 namespace hw {
 
+static_assert(kT2 == kTile2, "host tile table and kernel tile size differ");
+
 // Lax-Friedrichs fluxes of the pass-frame x physics at one point:
 // f, f'(u) v (normal moment), f'(u) w (tangential moment).
 template <typename T, int NC, int EQ>
@@ -52,13 +54,16 @@ __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, 
 // One directional pass for the lane's cell at box index bidx.  Returns the
 // Gauss-summed fluxes of the cell's low face (frame components) and the
 // limited derivative along the pass normal.  All 32 lanes must call it.
-template <typename T, int EQ, bool CHR, int D, bool W64>
-__device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, const WeightsT<T>& w,
+// The direction D (0: x pass, 1: y pass on the transposed stencil) is a
+// runtime value: both passes run this one copy of the code, which halves the
+// kernel's instruction footprint (instruction fetch was its top stall).
+template <typename T, int EQ, bool CHR, bool W64>
+__device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, int D, const WeightsT<T>& w,
                                        const WeightsT<double>& w64, bool lin, T ihn, T iht, T alpha, T g, T adv,
                                        T* Fu, T* Fv, T* Fw, T* vh) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
-  constexpr int SN = D == 0 ? 1 : kBP;
-  constexpr int ST = D == 0 ? kBP : 1;
+  const int SN = D == 0 ? 1 : kBP;
+  const int ST = D == 0 ? kBP : 1;
   const int o9[9] = {-SN - ST, -ST, SN - ST, -SN, 0, SN, -SN + ST, ST, SN + ST};
   const int o4[4] = {-SN, SN, -ST, ST};
   T cu[NC][15];
@@ -67,7 +72,7 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
   if (chr) {
     T x0[4];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) x0[k] = box[frame_field<D, EQ, NC>(0, k) * kFS + bidx];
+    for (int k = 0; k < NC; ++k) x0[k] = box[frame_field_rt<EQ, NC>(D, 0, k) * kFS + bidx];
     e = eig2<T>(x0[0], x0[1], x0[2], x0[3], g);
   }
   {
@@ -78,7 +83,7 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
       const int dd = s < 9 ? 0 : (s < 13 ? 1 : 2);
       const int off = s < 9 ? o9[s] : o4[(s - 9) & 3];
 #pragma unroll
-      for (int k = 0; k < NC; ++k) x[k] = box[frame_field<D, EQ, NC>(dd, k) * kFS + bidx + off];
+      for (int k = 0; k < NC; ++k) x[k] = box[frame_field_rt<EQ, NC>(D, dd, k) * kFS + bidx + off];
       if constexpr (CHR) {
         if (chr) {
           T y[4];
@@ -160,111 +165,105 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, cons
   }
 }
 
+// Per-tile quantities: kernel-wide for one grid, the tile's instance in a
+// batch (instance-relative state pointers, grid ratios, stage dt and alpha,
+// the boundary time).
+template <typename T>
+struct TileCtx {
+  const T* in;
+  const T* base;
+  T* out;
+  T* hat;
+  const unsigned char* smooth;
+  T idx, idy, dyx, dxy, tdt, ax, ay;
+  double t_bc;
+};
+
+// One 30 x 30 tile: halo box fill (ghosts resolved on the way in), x pass,
+// y pass and the RK stage update; the stage-3 spectral radius is folded
+// into radx / rady.
 template <typename T, int EQ, bool CHR, bool W64>
-__global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k_stage2d(const Stage2Args a) {
+__device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int i0, int j0, const TileCtx<T>& c,
+                                       T* box, T* stash, const WeightsT<T>& wx, const WeightsT<double>& wx64,
+                                       bool lin_all, T g, T advx_t, T advy_t, double& radx, double& rady) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   constexpr int NF = 3 * NC;
-  extern __shared__ __align__(16) unsigned char hw_smem[];
-  T* box = reinterpret_cast<T*>(hw_smem);
-  T* stash = box + NF * kFS;
-  const T* __restrict__ in = static_cast<const T*>(a.in);
-  const T* base = static_cast<const T*>(a.base);  // aliases out at stage 3
-  T* out = static_cast<T*>(a.out);
-  T* __restrict__ hat = static_cast<T*>(a.hat);
-  const Grid2& G = a.grid;
   const long long plane = a.plane;
-  if (a.stage != 0 && a.ctl->done) return;
-  // time of the stage for time-dependent boundaries: t^n, t^n + dt, t^n + dt/2
-  const double t_bc = a.stage <= 1 ? a.ctl->t : a.ctl->t + (a.stage == 2 ? 1.0 : 0.5) * a.ctl->dt;
-  const WeightsT<T> wx = make_weights<T>(a.wp);
-  WeightsT<T> wy = wx;  // transposed frame: S2 <-> S4
-  wy.g[2] = wx.g[4];
-  wy.g[4] = wx.g[2];
-  const WeightsT<double> wx64 = make_weights<double>(a.wp);
-  WeightsT<double> wy64 = wx64;
-  wy64.g[2] = wx64.g[4];
-  wy64.g[4] = wx64.g[2];
-  const bool lin_all = a.wp.linear != 0;
-  const unsigned char* __restrict__ smooth = a.smooth;
-  // scalars in T; the FP32 kernels take the host-rounded FP32 copies (a
-  // conversion the compiler re-did at each use would run on the FP64 pipe)
-  T g, idx, idy, dyx, dxy, tdt, ax_t, ay_t, advx_t, advy_t;
-  if constexpr (sizeof(T) == 4) {
-    g = a.f32.gamma_gas; idx = a.f32.idx; idy = a.f32.idy; dyx = a.f32.dyx; dxy = a.f32.dxy;
-    advx_t = a.f32.adv_x; advy_t = a.f32.adv_y;
-    if (a.stage == 0) {
-      tdt = T(0); ax_t = a.f32.ax_op; ay_t = a.f32.ay_op;
-    } else {
-      tdt = a.ctl->dtf; ax_t = a.ctl->axf; ay_t = a.ctl->ayf;
-    }
-  } else {
-    g = a.gamma_gas; idx = 1.0 / G.dx; idy = 1.0 / G.dy; dyx = G.dy / G.dx; dxy = G.dx / G.dy;
-    advx_t = a.adv_x; advy_t = a.adv_y;
-    if (a.stage == 0) {
-      tdt = T(0); ax_t = a.ax_op; ay_t = a.ay_op;
-    } else {
-      tdt = a.ctl->dt; ax_t = a.ctl->ax; ay_t = a.ctl->ay;
-    }
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  const int tiles_x = (G.nx + kT2 - 1) / kT2;
-  const int ntiles = tiles_x * ((G.ny + kT2 - 1) / kT2);
-  double radx = 0.0, rady = 0.0;
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int i0 = (tile % tiles_x) * kT2, j0 = (tile / tiles_x) * kT2;
-    __syncthreads();
-    const bool inner = i0 >= 2 && j0 >= 2 && i0 + kBox - 2 <= G.nx && j0 + kBox - 2 <= G.ny;
-    if (a.stage >= 2) {
-      // The y pass's stage update reads base and hat at the tile's cells:
-      // start pulling those rows into L2 now (3 points cover every 128-byte
-      // line of a 30-cell row in either precision).
-      for (int e = threadIdx.x; e < 3 * NC * kT2 * 3; e += blockDim.x) {
-        const int pl = e / (kT2 * 3), rem = e - pl * (kT2 * 3);
-        const int rr = rem / 3, pt = rem - rr * 3;
-        const int j = min(j0 + rr, G.ny - 1), i = min(i0 + (pt == 0 ? 0 : (pt == 1 ? 15 : kT2 - 1)), G.nx - 1);
-        const T* src = pl < NC ? base + pl * plane : hat + (pl - NC) * plane;
-        prefetch_l2(src + (long long)j * G.nx + i);
-      }
+  __syncthreads();
+  const T* __restrict__ in = c.in;
+  const T* base = c.base;
+  T* out = c.out;
+  T* __restrict__ hat = c.hat;
+  const unsigned char* __restrict__ smooth = c.smooth;
+  const T idx = c.idx, idy = c.idy, dyx = c.dyx, dxy = c.dxy, tdt = c.tdt;
+  const bool inner = i0 >= 2 && j0 >= 2 && i0 + kBox - 2 <= G.nx && j0 + kBox - 2 <= G.ny;
+  if (a.stage >= 2) {
+    // The y pass's stage update reads base and hat at the tile's cells:
+    // start pulling those rows into L2 now (3 points cover every 128-byte
+    // line of a 30-cell row in either precision).
+    for (int e = threadIdx.x; e < 3 * NC * kT2 * 3; e += blockDim.x) {
+      const int pl = e / (kT2 * 3), rem = e - pl * (kT2 * 3);
+      const int rr = rem / 3, pt = rem - rr * 3;
+      const int j = min(j0 + rr, G.ny - 1), i = min(i0 + (pt == 0 ? 0 : (pt == 1 ? 15 : kT2 - 1)), G.nx - 1);
+      const T* src = pl < NC ? base + pl * plane : hat + (pl - NC) * plane;
+      prefetch_l2(src + (long long)j * G.nx + i);
     }
-    if (inner) {
-      // whole box in flight at once; ghost-free, so a plain copy: a warp per
-      // box row (34 cells: lanes 0-31, then lanes 0-1 for the last two)
-      const T* src0 = in + (long long)(j0 - 2) * G.nx + (i0 - 2);
-      for (int row = warp; row < NF * kBox; row += nwarps) {
-        const int f = row / kBox, rr = row - f * kBox;
-        const T* srow = src0 + f * plane + (long long)rr * G.nx;
-        T* drow = box + f * kFS + rr * kBP;
-        cp_async_elem(drow + lane, srow + lane);
-        if (lane < kBox - 32) cp_async_elem(drow + 32 + lane, srow + 32 + lane);
-      }
-      cp_async_wait_all();
-    } else {
-      for (int e = threadIdx.x; e < NF * kBox * kBox; e += blockDim.x) {
-        const int f = e / (kBox * kBox), rem = e - f * (kBox * kBox);
-        const int rr = rem / kBox, cc = rem - rr * kBox;
-        const int i = min(max(i0 - 2 + cc, -2), G.nx + 1), j = min(max(j0 - 2 + rr, -2), G.ny + 1);
-        T v;
-        if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
-        else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j, t_bc);
-        box[f * kFS + rr * kBP + cc] = v;
-      }
+  }
+  if (inner) {
+    // whole box in flight at once; ghost-free, so a plain copy: a warp per
+    // box row (34 cells: lanes 0-31, then lanes 0-1 for the last two)
+    const T* src0 = in + (long long)(j0 - 2) * G.nx + (i0 - 2);
+    for (int row = warp; row < NF * kBox; row += nwarps) {
+      const int f = row / kBox, rr = row - f * kBox;
+      const T* srow = src0 + f * plane + (long long)rr * G.nx;
+      T* drow = box + f * kFS + rr * kBP;
+      cp_async_elem(drow + lane, srow + lane);
+      if (lane < kBox - 32) cp_async_elem(drow + 32 + lane, srow + 32 + lane);
     }
-    __syncthreads();
+    cp_async_wait_all();
+  } else {
+    for (int e = threadIdx.x; e < NF * kBox * kBox; e += blockDim.x) {
+      const int f = e / (kBox * kBox), rem = e - f * (kBox * kBox);
+      const int rr = rem / kBox, cc = rem - rr * kBox;
+      const int i = min(max(i0 - 2 + cc, -2), G.nx + 1), j = min(max(j0 - 2 + rr, -2), G.ny + 1);
+      T v;
+      if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
+      else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j, c.t_bc);
+      box[f * kFS + rr * kBP + cc] = v;
+    }
+  }
+  __syncthreads();
 
-    // ---- x pass: one row per warp iteration, lane l <-> cell i0-1+l ----
+  // ---- x pass (D = 0): one row per warp iteration, lane l <-> cell i0-1+l;
+  // ---- y pass (D = 1) on the transposed box: one column per iteration.
+#pragma unroll 1
+  for (int D = 0; D < 2; ++D) {
+    if (D == 1) __syncthreads();  // the x pass's stash is complete
+    const int lines = D == 0 ? G.ny - j0 : G.nx - i0;
     for (int r = warp; r < kT2; r += nwarps) {
-      if (j0 + r >= G.ny) break;
+      if (r >= lines) break;
       // learned indicator: a warp whose 32 cells are all smooth takes p0
       bool lin = lin_all;
       if (smooth != nullptr && !lin) {
-        const int ic = min(max(i0 - 1 + lane, 0), G.nx - 1);
-        lin = __all_sync(HW_FULL_MASK, smooth[(long long)(j0 + r) * G.nx + ic] != 0);
+        const int ii = D == 0 ? min(max(i0 - 1 + lane, 0), G.nx - 1) : i0 + r;
+        const int jj = D == 0 ? j0 + r : min(max(j0 - 1 + lane, 0), G.ny - 1);
+        lin = __all_sync(HW_FULL_MASK, smooth[(long long)jj * G.nx + ii] != 0);
+      }
+      const int bidx = D == 0 ? (r + 2) * kBP + lane + 1 : (lane + 1) * kBP + r + 2;
+      // the pass's weights by value (S2 <-> S4 in the transposed frame)
+      WeightsT<T> wp = wx;
+      wp.g[2] = D == 0 ? wx.g[2] : wx.g[4];
+      wp.g[4] = D == 0 ? wx.g[4] : wx.g[2];
+      WeightsT<double> wp64 = wx64;
+      if constexpr (W64) {
+        wp64.g[2] = D == 0 ? wx64.g[2] : wx64.g[4];
+        wp64.g[4] = D == 0 ? wx64.g[4] : wx64.g[2];
       }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 0, W64>(box, (r + 2) * kBP + lane + 1, wx, wx64, lin, idx, idy, ax_t, g, advx_t, Fu,
-                                 Fv, Fw, vh);
+      pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
+                              D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh);
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -272,41 +271,23 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
         Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
         Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
       }
-      if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
-        const int sidx = stash_at<T>(r, lane - 1);
+      if (D == 0) {
+        if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
+          const int sidx = stash_at<T>(r, lane - 1);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          stash[(0 * NC + k) * kSS + sidx] = -(Gu[k] - Fu[k]) * idx;
-          stash[(1 * NC + k) * kSS + sidx] = -(Gv[k] - Fv[k]);
-          stash[(2 * NC + k) * kSS + sidx] = -(Gw[k] - Fw[k]) * dyx;
-          stash[(3 * NC + k) * kSS + sidx] = vh[k];
+          for (int k = 0; k < NC; ++k) {
+            stash[(0 * NC + k) * kSS + sidx] = -(Gu[k] - Fu[k]) * idx;
+            stash[(1 * NC + k) * kSS + sidx] = -(Gv[k] - Fv[k]);
+            stash[(2 * NC + k) * kSS + sidx] = -(Gw[k] - Fw[k]) * dyx;
+            stash[(3 * NC + k) * kSS + sidx] = vh[k];
+          }
         }
+        continue;
       }
-    }
-    __syncthreads();
-
-    // ---- y pass on the transposed box: one column per warp iteration ----
-    for (int c = warp; c < kT2; c += nwarps) {
-      const int i = i0 + c;
-      if (i >= G.nx) break;
-      bool lin = lin_all;
-      if (smooth != nullptr && !lin) {
-        const int jc = min(max(j0 - 1 + lane, 0), G.ny - 1);
-        lin = __all_sync(HW_FULL_MASK, smooth[(long long)jc * G.nx + i] != 0);
-      }
-      T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, 1, W64>(box, (lane + 1) * kBP + c + 2, wy, wy64, lin, idy, idx, ay_t, g, advy_t, Fu,
-                                 Fv, Fw, vh);
-      T Gu[NC], Gv[NC], Gw[NC];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
-        Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
-        Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
-      }
+      const int cc = r, i = i0 + cc;
       const int j = j0 - 1 + lane;
       if (lane >= 1 && lane <= kT2 && j < G.ny) {
-        const int sidx = stash_at<T>(lane - 1, c);
+        const int sidx = stash_at<T>(lane - 1, cc);
         const long long p = (long long)j * G.nx + i;
         T nu[NC];
 #pragma unroll
@@ -323,7 +304,7 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
             out[iu] = Lu; out[iv] = Lv; out[iw] = Lw;
             hat[hv] = vx; hat[hw_] = wyv;
           } else {
-            const T ub = box[k * kFS + (lane + 1) * kBP + c + 2];
+            const T ub = box[k * kFS + (lane + 1) * kBP + cc + 2];
             const T su = ub + tdt * Lu, sv = vx + tdt * Lv, sw = wyv + tdt * Lw;
             if (a.stage == 1) {
               out[iu] = su; out[iv] = sv; out[iw] = sw;
@@ -359,21 +340,127 @@ __global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k
       }
     }
   }
-  if (a.stage == 3) {
-    radx = warp_max(radx);
-    rady = warp_max(rady);
-    if (lane == 0) {
-      atomic_max_nonneg(&a.ctl->amax_x, radx);
-      atomic_max_nonneg(&a.ctl->amax_y, rady);
+}
+
+// FAST: the paper's configuration (moment indicator, beta + eps) fixed at
+// compile time, so no code of the variants is predicated into the hot path
+// (4% fewer FP64-pipe instructions in the mixed kernel than with the
+// run-time switches).  BATCH: the tiles of many 2D instances of uneven sizes
+// (a tile table; per-instance descriptors and control blocks).
+template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
+__global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k_stage2d(const Stage2Args a) {
+  constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
+  constexpr int NF = 3 * NC;
+  extern __shared__ __align__(16) unsigned char hw_smem[];
+  T* box = reinterpret_cast<T*>(hw_smem);
+  T* stash = box + NF * kFS;
+  WeightsT<T> wx = make_weights<T>(a.wp);
+  WeightsT<double> wx64 = make_weights<double>(a.wp);
+  if constexpr (FAST) {
+    wx.pow2 = 0;
+    wx.typical = 0;
+    wx64.pow2 = 0;
+    wx64.typical = 0;
+  }
+  const bool lin_all = a.wp.linear != 0;
+  // scalars in T; the FP32 kernels take the host-rounded FP32 copies (a
+  // conversion the compiler re-did at each use would run on the FP64 pipe)
+  T g, advx_t, advy_t;
+  if constexpr (sizeof(T) == 4) {
+    g = a.f32.gamma_gas; advx_t = a.f32.adv_x; advy_t = a.f32.adv_y;
+  } else {
+    g = a.gamma_gas; advx_t = a.adv_x; advy_t = a.adv_y;
+  }
+  const int lane = threadIdx.x & 31;
+  double radx = 0.0, rady = 0.0;
+  TileCtx<T> c;
+  c.smooth = a.smooth;
+
+  if constexpr (!BATCH) {
+    const Grid2& G = a.grid;
+    if (a.stage != 0 && a.ctl->done) return;
+    // time of the stage for time-dependent boundaries: t^n, t^n + dt, t^n + dt/2
+    c.t_bc = a.stage <= 1 ? a.ctl->t : a.ctl->t + (a.stage == 2 ? 1.0 : 0.5) * a.ctl->dt;
+    c.in = static_cast<const T*>(a.in);
+    c.base = static_cast<const T*>(a.base);  // aliases out at stage 3
+    c.out = static_cast<T*>(a.out);
+    c.hat = static_cast<T*>(a.hat);
+    if constexpr (sizeof(T) == 4) {
+      c.idx = a.f32.idx; c.idy = a.f32.idy; c.dyx = a.f32.dyx; c.dxy = a.f32.dxy;
+      if (a.stage == 0) {
+        c.tdt = T(0); c.ax = a.f32.ax_op; c.ay = a.f32.ay_op;
+      } else {
+        c.tdt = a.ctl->dtf; c.ax = a.ctl->axf; c.ay = a.ctl->ayf;
+      }
+    } else {
+      c.idx = 1.0 / G.dx; c.idy = 1.0 / G.dy; c.dyx = G.dy / G.dx; c.dxy = G.dx / G.dy;
+      if (a.stage == 0) {
+        c.tdt = T(0); c.ax = a.ax_op; c.ay = a.ay_op;
+      } else {
+        c.tdt = a.ctl->dt; c.ax = a.ctl->ax; c.ay = a.ctl->ay;
+      }
+    }
+    const int tiles_x = (G.nx + kT2 - 1) / kT2;
+    const int ntiles = tiles_x * ((G.ny + kT2 - 1) / kT2);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int i0 = (tile % tiles_x) * kT2, j0 = (tile / tiles_x) * kT2;
+      tile2d<T, EQ, CHR, W64>(a, G, i0, j0, c, box, stash, wx, wx64, lin_all, g, advx_t, advy_t, radx, rady);
+    }
+    if (a.stage == 3) {
+      radx = warp_max(radx);
+      rady = warp_max(rady);
+      if (lane == 0) {
+        atomic_max_nonneg(&a.ctl->amax_x, radx);
+        atomic_max_nonneg(&a.ctl->amax_y, rady);
+      }
+    }
+  } else {
+    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+      const Tile2 tl = a.tiles[tile];
+      const Inst2& I = a.inst[tl.inst];
+      Ctl* ctl = a.ctl + tl.inst;
+      if (a.stage != 0 && ctl->done) continue;  // the same for the whole CTA
+      c.t_bc = a.stage <= 1 ? ctl->t : ctl->t + (a.stage == 2 ? 1.0 : 0.5) * ctl->dt;
+      c.in = static_cast<const T*>(a.in) + I.off;
+      c.base = static_cast<const T*>(a.base) + I.off;
+      c.out = static_cast<T*>(a.out) + I.off;
+      c.hat = static_cast<T*>(a.hat) + I.off;
+      if constexpr (sizeof(T) == 4) {
+        c.idx = I.idxf; c.idy = I.idyf; c.dyx = I.dyxf; c.dxy = I.dxyf;
+        if (a.stage == 0) {
+          c.tdt = T(0); c.ax = (T)a.alpha_op[2 * tl.inst]; c.ay = (T)a.alpha_op[2 * tl.inst + 1];
+        } else {
+          c.tdt = ctl->dtf; c.ax = ctl->axf; c.ay = ctl->ayf;
+        }
+      } else {
+        c.idx = I.idx; c.idy = I.idy; c.dyx = I.dyx; c.dxy = I.dxy;
+        if (a.stage == 0) {
+          c.tdt = T(0); c.ax = a.alpha_op[2 * tl.inst]; c.ay = a.alpha_op[2 * tl.inst + 1];
+        } else {
+          c.tdt = ctl->dt; c.ax = ctl->ax; c.ay = ctl->ay;
+        }
+      }
+      tile2d<T, EQ, CHR, W64>(a, I.grid, tl.i0, tl.j0, c, box, stash, wx, wx64, lin_all, g, advx_t, advy_t, radx,
+                              rady);
+      if (a.stage == 3) {  // this tile's instance
+        radx = warp_max(radx);
+        rady = warp_max(rady);
+        if (lane == 0) {
+          atomic_max_nonneg(&ctl->amax_x, radx);
+          atomic_max_nonneg(&ctl->amax_y, rady);
+        }
+        radx = 0.0;
+        rady = 0.0;
+      }
     }
   }
 }
 
 template <typename T, int EQ>
-__global__ void __launch_bounds__(256) k_alpha2d(const T* __restrict__ U, long long plane, double gamma_gas,
-                                                 double adv_x, double adv_y, Ctl* ctl) {
+__global__ void __launch_bounds__(256) k_alpha2d(const T* __restrict__ U, long long count, long long plane,
+                                                 double gamma_gas, double adv_x, double adv_y, Ctl* ctl) {
   double rx = 0.0, ry = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < plane;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < count;
        c += (long long)gridDim.x * blockDim.x) {
     double a, b;
     if constexpr (EQ == HWENO_EQ_EULER) {
@@ -398,18 +485,19 @@ __global__ void __launch_bounds__(256) k_alpha2d(const T* __restrict__ U, long l
   }
 }
 
-template <typename T, int EQ, bool CHR, bool W64>
+template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
 struct Launch2 {
   static int per_sm;  // resident CTAs per SM, 0 until prepared
   static cudaError_t prepare() {
     if (per_sm > 0) return cudaSuccess;
     constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
     constexpr size_t smem = smem_bytes2<T, NC>();
-    cudaError_t e = cudaFuncSetAttribute(k_stage2d<T, EQ, CHR, W64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_stage2d<T, EQ, CHR, W64, FAST, BATCH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR, W64>, kThreads2, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR, W64, FAST, BATCH>, kThreads2,
+                                                      smem);
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
     per_sm = n;
@@ -422,35 +510,56 @@ struct Launch2 {
       cudaError_t e = prepare();
       if (e != cudaSuccess) return e;
     }
-    const long long tiles = (long long)((a.grid.nx + kT2 - 1) / kT2) * ((a.grid.ny + kT2 - 1) / kT2);
+    const long long tiles =
+        BATCH ? a.ntiles : (long long)((a.grid.nx + kT2 - 1) / kT2) * ((a.grid.ny + kT2 - 1) / kT2);
+    if (tiles < 1) return cudaSuccess;
     long long blocks = sh.persistent2d ? (long long)num_sms * per_sm : tiles;
     if (blocks > tiles) blocks = tiles;
-    k_stage2d<T, EQ, CHR, W64><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
+    k_stage2d<T, EQ, CHR, W64, FAST, BATCH><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
     return cudaGetLastError();
   }
 };
-template <typename T, int EQ, bool CHR, bool W64>
-int Launch2<T, EQ, CHR, W64>::per_sm = 0;
+template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
+int Launch2<T, EQ, CHR, W64, FAST, BATCH>::per_sm = 0;
+
+// The compile-time fast form exists for the characteristic-wise Euler
+// kernels (the workloads' path); every other combination runs the
+// run-time switches.
+inline bool fast_form(const WeightParams& wp) { return wp.pow2 == 0 && wp.typical == 0; }
 
 template <typename T, int EQ, bool CHR, bool W64 = false>
 static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st, const LaunchShape& sh) {
-  return Launch2<T, EQ, CHR, W64>::go(a, num_sms, st, sh);
+  if (a.batched) return Launch2<T, EQ, CHR, W64, false, true>::go(a, num_sms, st, sh);
+  if constexpr (EQ == HWENO_EQ_EULER && CHR) {
+    if (fast_form(a.wp)) return Launch2<T, EQ, CHR, W64, true, false>::go(a, num_sms, st, sh);
+  }
+  return Launch2<T, EQ, CHR, W64, false, false>::go(a, num_sms, st, sh);
 }
 
-template <typename T, bool W64>
-static cudaError_t prep2(int equation, bool chr) {
-  if (equation == HWENO_EQ_EULER)
-    return chr ? Launch2<T, HWENO_EQ_EULER, true, W64>::prepare() : Launch2<T, HWENO_EQ_EULER, false, W64>::prepare();
-  if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false, W64>::prepare();
-  return Launch2<T, HWENO_EQ_ADVECTION, false, W64>::prepare();
+template <typename T, bool W64, bool BATCH>
+static cudaError_t prep2(int equation, bool chr, bool fast) {
+  if (equation == HWENO_EQ_EULER) {
+    if (chr)
+      return fast && !BATCH ? Launch2<T, HWENO_EQ_EULER, true, W64, true, false>::prepare()
+                            : Launch2<T, HWENO_EQ_EULER, true, W64, false, BATCH>::prepare();
+    return Launch2<T, HWENO_EQ_EULER, false, W64, false, BATCH>::prepare();
+  }
+  if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false, W64, false, BATCH>::prepare();
+  return Launch2<T, HWENO_EQ_ADVECTION, false, W64, false, BATCH>::prepare();
 }
 
-cudaError_t prepare_stage2d(int precision, int equation, int charwise) {
+cudaError_t prepare_stage2d(int precision, int equation, int charwise, const WeightParams& wp, bool batched) {
   const bool chr = equation == HWENO_EQ_EULER && charwise;
+  const bool fast = fast_form(wp);
   // the linear-weight path of a characteristic solver runs the same kernel
-  if (precision == HWENO_FP64) return prep2<double, false>(equation, chr);
-  if (precision == HWENO_FP32_IND64) return prep2<float, true>(equation, chr);
-  return prep2<float, false>(equation, chr);
+  if (batched) {
+    if (precision == HWENO_FP64) return prep2<double, false, true>(equation, chr, fast);
+    if (precision == HWENO_FP32_IND64) return prep2<float, true, true>(equation, chr, fast);
+    return prep2<float, false, true>(equation, chr, fast);
+  }
+  if (precision == HWENO_FP64) return prep2<double, false, false>(equation, chr, fast);
+  if (precision == HWENO_FP32_IND64) return prep2<float, true, false>(equation, chr, fast);
+  return prep2<float, false, false>(equation, chr, fast);
 }
 
 cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stage2Args& a, int num_sms,
@@ -474,13 +583,13 @@ cudaError_t launch_stage2d(int precision, int equation, int charwise, const Stag
   return go2<float, HWENO_EQ_ADVECTION, false>(a, num_sms, st, sh);
 }
 
-cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long plane, double gamma_gas,
-                           double adv_x, double adv_y, Ctl* ctl, int num_sms, cudaStream_t st) {
-  long long blocks = (plane + 255) / 256;
+cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long count, long long plane,
+                           double gamma_gas, double adv_x, double adv_y, Ctl* ctl, int num_sms, cudaStream_t st) {
+  long long blocks = (count + 255) / 256;
   if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
   if (blocks < 1) blocks = 1;
 #define HW_A2(T, EQ) k_alpha2d<T, EQ><<<(unsigned)blocks, 256, 0, st>>>( \
-    static_cast<const T*>(U), plane, gamma_gas, adv_x, adv_y, ctl)
+    static_cast<const T*>(U), count, plane, gamma_gas, adv_x, adv_y, ctl)
   if (precision == HWENO_FP64) {
     if (equation == HWENO_EQ_EULER) HW_A2(double, HWENO_EQ_EULER);
     else if (equation == HWENO_EQ_BURGERS) HW_A2(double, HWENO_EQ_BURGERS);

@@ -557,7 +557,8 @@ class Solver:
 
 
 class Batch:
-    """Independent 1D problems of uneven sizes, advanced together."""
+    """Independent problems of uneven sizes (all 1D or all 2D), advanced
+    together: one launch per RK stage covers every instance."""
 
     def __init__(self, cfgs, stream=None):
         import torch
@@ -585,12 +586,17 @@ class Batch:
         return hweno_batch_stream(self.h)
 
     def pack(self, states):
-        """Concatenate per-instance [nf, n_k] arrays into [nf, total]."""
-        return np.concatenate([np.asarray(s, dtype=np.float64) for s in states], axis=1)
+        """Concatenate per-instance [nf, n_k] (1D) or [nf, ny_k, nx_k] (2D)
+        arrays into [nf, total]."""
+        return np.concatenate([np.asarray(s, dtype=np.float64).reshape(self.nf, -1) for s in states], axis=1)
 
     def unpack(self, U):
         U = U.cpu().numpy() if hasattr(U, "cpu") else U
-        return [U[:, self.offsets[k]:self.offsets[k + 1]] for k in range(self.n)]
+        out = []
+        for k, c in enumerate(self.cfgs):
+            part = U[:, self.offsets[k]:self.offsets[k + 1]]
+            out.append(part.reshape(U.shape[0], c.ny, c.nx) if c.dim == 2 else part)
+        return out
 
     def set_state(self, U):
         if isinstance(U, np.ndarray):
@@ -615,9 +621,11 @@ class Batch:
         return hweno_batch_advance(self.h, t_final, max_steps)
 
     def apply_operator(self, alpha):
+        """alpha: per instance alpha (1D) or (alpha_x, alpha_y) pairs (2D)."""
         import torch
-        nc = self.cfgs[0].ncomp
+        c0 = self.cfgs[0]
         L = torch.empty((self.nf, self.total), dtype=self.dtype, device="cuda")
-        D = torch.empty((nc, self.total), dtype=self.dtype, device="cuda")
-        hweno_batch_apply_operator(self.h, alpha, L, D)
+        D = torch.empty((c0.ncomp * c0.dim, self.total), dtype=self.dtype, device="cuda")
+        flat = np.asarray(alpha, dtype=np.float64).reshape(-1)
+        hweno_batch_apply_operator(self.h, flat, L, D)
         return L, D

@@ -382,3 +382,18 @@ def dmr_2d(nx, ny, gamma=GAMMA) -> np.ndarray:
     sw = np.clip(np.minimum(xl + dx, xs_t) - np.maximum(xl, xs_b), 0.0, None) / dx
     wbar = (post - pre)[:, None, None] * sw[None]
     return np.concatenate([ubar, vbar, wbar], axis=0)
+
+
+def quadrant_batch_2d(n: int = 48, seed: int = 2025, nmin: int = 96, nmax: int = 768):
+    """Seeded batch of 2D four-quadrant Riemann problems on [0,1]^2 of uneven
+    sizes: nx, ny log-uniform in [nmin, nmax] independently, quadrant states
+    quadrant_states(seed + k), split point U[0.3, 0.7]^2.  Returns (sizes
+    [(nx, ny)], states [U_k])."""
+    rng = np.random.default_rng(seed)
+    nx = np.clip(np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=n)).astype(np.int64), nmin, nmax)
+    ny = np.clip(np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=n)).astype(np.int64), nmin, nmax)
+    split = rng.uniform(0.3, 0.7, size=(n, 2))
+    sizes = [(int(nx[k]), int(ny[k])) for k in range(n)]
+    states = [quadrant_2d(quadrant_states(seed + k), split[k, 0], split[k, 1], 0.0, 1.0, 0.0, 1.0, *sizes[k])
+              for k in range(n)]
+    return sizes, states

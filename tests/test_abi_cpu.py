@@ -92,5 +92,10 @@ def test_batch_rejects_mixed_parameters():
     assert hw.load().hweno_batch_create(2, arr, None, C.byref(h)) == hw.HWENO_ERR_ARG
     assert "batch-wide" in hw.hweno_last_error()
     c2 = hw.Config(dim=2, nx=8, ny=8, lin_w=(0.99, 0.0025, 0.0025, 0.0025, 0.0025))
-    arr2 = (hw.hweno_config * 1)(c2.to_c())
-    assert hw.load().hweno_batch_create(1, arr2, None, C.byref(h)) == hw.HWENO_ERR_ARG
+    arr2 = (hw.hweno_config * 2)(c2.to_c(), a.to_c())
+    assert hw.load().hweno_batch_create(2, arr2, None, C.byref(h)) == hw.HWENO_ERR_ARG
+    assert "same dim" in hw.hweno_last_error()
+    c3 = hw.Config(dim=2, nx=8, ny=8, lin_w=(0.98, 0.005, 0.005, 0.005, 0.005))
+    arr3 = (hw.hweno_config * 2)(c2.to_c(), c3.to_c())
+    assert hw.load().hweno_batch_create(2, arr3, None, C.byref(h)) == hw.HWENO_ERR_ARG
+    assert "batch-wide" in hw.hweno_last_error()
