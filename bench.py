@@ -46,13 +46,13 @@ ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64",
         ("fp32_learned", "FP32", True, {}), ("fp32_ind64_learned", "FP32_IND64", True, {}),
         ("fp32_ind64_typical", "FP32_IND64", False, {"smoothness": "BETA_TYPICAL"}),
         ("fp32_ind64_component", "FP32_IND64", False, {"charwise": 0})]
-FLOPS_PER_CELL_STAGE = {"fp64": 5734.0, "fp32": 5307.0, "fp32_ind64": 1297.0}
+FLOPS_PER_CELL_STAGE = {"fp64": 5712.0, "fp32": 5313.0, "fp32_ind64": None}
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
                 "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); the "
                 "mixed kernel counts its FP64 flops (its bound)")
 # DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
 # the bench grid by cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 652.5e6 / 1536 ** 2, "fp32": 339.7e6 / 1536 ** 2, "fp32_ind64": 319.1e6 / 1536 ** 2}
+TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 335.3e6 / 1536 ** 2, "fp32_ind64": None}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 1536^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)

@@ -259,8 +259,8 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
 //    rcp_newton); a_m rounded to FP32 and the normalisation of
 //    w~_m = gamma_m (1 + a_m) in FP32: every term is positive, so it adds
 //    no more than a few FP32 ulp to the weights, which are FP32 anyway.
-__device__ __forceinline__ void weights2_ind64(const float* q, const WeightsT<double>& w, const WeightsT<float>& wf,
-                                               float& r, float* om) {
+__device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
+                                               const WeightsT<float>& wf, float& r, float* om) {
   const float q5f = q[4];
   float d32[9];
   bool exact = true;
@@ -272,59 +272,111 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const WeightsT<do
     exact = exact && ((a - (sum - bb)) + (b - bb)) == 0.0f;
     d32[s] = sum;
   }
-  double d[9];
-  if (__all_sync(HW_FULL_MASK, exact)) {
+  // FP32 screen: a sound upper bound on every a_m = tau^2 / (beta_m^p + eps)
+  // from the FP32 coefficients k.  Each c~_l combines the stencil differences
+  // and moments (largest magnitude S) and errs by at most ~30 u S in FP32
+  // (u = 2^-24), bounded here by E = 2^-16 S; hence
+  //   |beta~_0 - beta_0| <= 2^-19 beta~_0 + E (2 sum_l w_l |c~_l| + 1331 E),
+  //   |beta~_m - beta_m| <= 2^-20 beta~_m  (m >= 1),
+  // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  Where the
+  // bound puts every a_m below 2^-28 for all 32 lanes, 1 + a_m is 1 in FP32
+  // whatever the FP64 evaluation gives, so that evaluation is skipped and
+  // the result is the same bit for bit.
+  bool quiet = !w.typical;  // the bound is written for the moment form
+  if (quiet) {
+    float S = 0.0f;
 #pragma unroll
     for (int s = 0; s < 9; ++s)
-      if (s != 4) d[s] = widen_f32(d32[s]);
-  } else {
-    const double q5 = widen_f32(q5f);
+      if (s != 4) S = fmaxf(S, fabsf(d32[s]));
 #pragma unroll
-    for (int s = 0; s < 9; ++s)
-      if (s != 4) d[s] = widen_f32(q[s]) - q5;
+    for (int s = 9; s < 17; ++s) S = fmaxf(S, fabsf(q[s]));
+    const float* c = k.c;
+    const float sw = (fabsf(c[1]) + fabsf(c[2]) + fabsf(c[4])) +
+                     4.0f * (fabsf(c[3]) + fabsf(c[5]) + fabsf(c[7]) + fabsf(c[8])) +
+                     36.0f * (fabsf(c[6]) + fabsf(c[9]) + fabsf(c[11]) + fabsf(c[13])) +
+                     576.0f * (fabsf(c[10]) + fabsf(c[14])) + 16.0f * fabsf(c[12]);
+    float bs[5];
+    bs[0] = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] + 4.0f * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
+            36.0f * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
+            576.0f * (c[10] * c[10] + c[14] * c[14]) + 16.0f * c[12] * c[12];
+    bs[1] = k.dW * k.dW + k.dS * k.dS;
+    bs[2] = k.dE * k.dE + k.dS * k.dS;
+    bs[3] = k.dE * k.dE + k.dN * k.dN;
+    bs[4] = k.dW * k.dW + k.dN * k.dN;
+    const float E = S * 0x1p-16f;
+    float Ds[5];
+    Ds[0] = 0x1p-19f * bs[0] + E * (2.0f * sw + 1331.0f * E);
+#pragma unroll
+    for (int m = 1; m < 5; ++m) Ds[m] = 0x1p-20f * bs[m];
+    const float tau = 0.25f * ((fabsf(bs[0] - bs[1]) + fabsf(bs[0] - bs[2])) +
+                               (fabsf(bs[0] - bs[3]) + fabsf(bs[0] - bs[4])));
+    const float ut = tau * (1.0f + 0x1p-20f) + Ds[0] + 0.25f * ((Ds[1] + Ds[2]) + (Ds[3] + Ds[4]));
+    const float ut2 = ut * ut;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const float L = fmaxf(bs[m] - Ds[m], 0.0f);
+      const float dlo = (wf.pow2 ? L * L : L) + wf.eps;
+      quiet = quiet && ut2 < 0x1p-28f * dlo;
+    }
   }
-  const double d1 = d[0], d2 = d[1], d3 = d[2], d4 = d[3], d6 = d[5], d7 = d[6], d8 = d[7], d9 = d[8];
-  const double q10 = widen_f32(q[9]), q11 = widen_f32(q[10]), q12 = widen_f32(q[11]), q13 = widen_f32(q[12]);
-  const double q14 = widen_f32(q[13]), q15 = widen_f32(q[14]), q16 = widen_f32(q[15]), q17 = widen_f32(q[16]);
-  const double s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
-  const double sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
-  const double ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
-  const double s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
-  const double s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
-  const double u1 = 2.0 * ax + 19.0 * dxe - 6.0 * s1011 + 3.0 * s1213;
-  const double u2 = 2.0 * ay + 19.0 * dye + 3.0 * s1415 - 6.0 * s1617;
-  const double u3 = 2.0 * ey - sc + 62.0 * ex - 18.0 * m1110;
-  const double u5 = 2.0 * ex - sc + 62.0 * ey - 18.0 * m1716;
-  const double u4 = 3.0 * cx + 5.0 * (m1213 + m1415);
-  const double u6 = 4.0 * (s1011 - dxe) - ax - 2.0 * s1213;
-  const double u9 = 4.0 * (s1617 - dye) - ay - 2.0 * s1415;
-  const double u7 = ay + 2.0 * dye, u8 = ax + 2.0 * dxe;
-  const double u10 = m1110 - 2.0 * ex, u14 = m1716 - 2.0 * ey;
-  const double u11 = cx + 2.0 * m1213, u13 = cx + 2.0 * m1415;
-  const double u12 = sc - 2.0 * (ex + ey);
-  double b0;
-  if (w.typical) {  // the Jiang-Shu form needs the scaled coefficients c_l = u_l / den_l
-    const double c[15] = {0.0,         u1 * (1.0 / 24.0), u2 * (1.0 / 24.0), u3 * (1.0 / 48.0), -0.125 * u4,
-                          u5 * (1.0 / 48.0), 0.05 * u6,   -0.25 * u7,        -0.25 * u8,        0.05 * u9,
-                          0.25 * u10,  0.25 * u11,        0.25 * u12,        0.25 * u13,        0.25 * u14};
-    b0 = beta_typical_2d(c);
-  } else {
-    double acc = u1 * u1 + u2 * u2 + u3 * u3 + u5 * u5 + 9.0 * u4 * u4;
-    acc += 144.0 * (u7 * u7 + u8 * u8) + 51.84 * (u6 * u6 + u9 * u9);
-    acc += 1296.0 * (u11 * u11 + u13 * u13) + 20736.0 * (u10 * u10 + u14 * u14) + 576.0 * u12 * u12;
-    b0 = acc * (1.0 / 576.0);
-  }
-  const double w2 = d4 * d4, e2 = d6 * d6, s2 = d2 * d2, n2 = d8 * d8;  // dW, dE, dS, dN squared
-  const double b1 = w2 + s2, b2 = e2 + s2, b3 = e2 + n2, b4 = w2 + n2;
-  const double tau = 0.25 * ((fabs(b0 - b1) + fabs(b0 - b2)) + (fabs(b0 - b3) + fabs(b0 - b4)));
-  // the epsilon-sensitive part in FP64: a_m = tau^2 / (beta_m^{1|2} + eps)
-  const double t2 = tau * tau;
-  const double beta[5] = {b0, b1, b2, b3, b4};
   float a[5];
+  if (__all_sync(HW_FULL_MASK, quiet)) {
 #pragma unroll
-  for (int m = 0; m < 5; ++m) {
-    const double dm = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
-    a[m] = narrow_f64_ftz(t2 * rcp_newton(dm));
+    for (int m = 0; m < 5; ++m) a[m] = 0.0f;
+  } else {
+    double d[9];
+    if (__all_sync(HW_FULL_MASK, exact)) {
+#pragma unroll
+      for (int s = 0; s < 9; ++s)
+        if (s != 4) d[s] = widen_f32(d32[s]);
+    } else {
+      const double q5 = widen_f32(q5f);
+#pragma unroll
+      for (int s = 0; s < 9; ++s)
+        if (s != 4) d[s] = widen_f32(q[s]) - q5;
+    }
+    const double d1 = d[0], d2 = d[1], d3 = d[2], d4 = d[3], d6 = d[5], d7 = d[6], d8 = d[7], d9 = d[8];
+    const double q10 = widen_f32(q[9]), q11 = widen_f32(q[10]), q12 = widen_f32(q[11]), q13 = widen_f32(q[12]);
+    const double q14 = widen_f32(q[13]), q15 = widen_f32(q[14]), q16 = widen_f32(q[15]), q17 = widen_f32(q[16]);
+    const double s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
+    const double sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
+    const double ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
+    const double s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
+    const double s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
+    const double u1 = 2.0 * ax + 19.0 * dxe - 6.0 * s1011 + 3.0 * s1213;
+    const double u2 = 2.0 * ay + 19.0 * dye + 3.0 * s1415 - 6.0 * s1617;
+    const double u3 = 2.0 * ey - sc + 62.0 * ex - 18.0 * m1110;
+    const double u5 = 2.0 * ex - sc + 62.0 * ey - 18.0 * m1716;
+    const double u4 = 3.0 * cx + 5.0 * (m1213 + m1415);
+    const double u6 = 4.0 * (s1011 - dxe) - ax - 2.0 * s1213;
+    const double u9 = 4.0 * (s1617 - dye) - ay - 2.0 * s1415;
+    const double u7 = ay + 2.0 * dye, u8 = ax + 2.0 * dxe;
+    const double u10 = m1110 - 2.0 * ex, u14 = m1716 - 2.0 * ey;
+    const double u11 = cx + 2.0 * m1213, u13 = cx + 2.0 * m1415;
+    const double u12 = sc - 2.0 * (ex + ey);
+    double b0;
+    if (w.typical) {  // the Jiang-Shu form needs the scaled coefficients c_l = u_l / den_l
+      const double c[15] = {0.0,         u1 * (1.0 / 24.0), u2 * (1.0 / 24.0), u3 * (1.0 / 48.0), -0.125 * u4,
+                            u5 * (1.0 / 48.0), 0.05 * u6,   -0.25 * u7,        -0.25 * u8,        0.05 * u9,
+                            0.25 * u10,  0.25 * u11,        0.25 * u12,        0.25 * u13,        0.25 * u14};
+      b0 = beta_typical_2d(c);
+    } else {
+      double acc = u1 * u1 + u2 * u2 + u3 * u3 + u5 * u5 + 9.0 * u4 * u4;
+      acc += 144.0 * (u7 * u7 + u8 * u8) + 51.84 * (u6 * u6 + u9 * u9);
+      acc += 1296.0 * (u11 * u11 + u13 * u13) + 20736.0 * (u10 * u10 + u14 * u14) + 576.0 * u12 * u12;
+      b0 = acc * (1.0 / 576.0);
+    }
+    const double w2 = d4 * d4, e2 = d6 * d6, s2 = d2 * d2, n2 = d8 * d8;  // dW, dE, dS, dN squared
+    const double b1 = w2 + s2, b2 = e2 + s2, b3 = e2 + n2, b4 = w2 + n2;
+    const double tau = 0.25 * ((fabs(b0 - b1) + fabs(b0 - b2)) + (fabs(b0 - b3) + fabs(b0 - b4)));
+    // the epsilon-sensitive part in FP64: a_m = tau^2 / (beta_m^{1|2} + eps)
+    const double t2 = tau * tau;
+    const double beta[5] = {b0, b1, b2, b3, b4};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const double dm = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
+      a[m] = narrow_f64_ftz(t2 * rcp_newton(dm));
+    }
   }
   // w~_m = gamma_m (1 + a_m) and the normalisation (well conditioned: all
   // terms positive) in FP32
@@ -353,7 +405,7 @@ __device__ __forceinline__ void recon2_w64(const float* q, const WeightsT<float>
     return;
   }
   float r, om[5];
-  weights2_ind64(q, w64, w, r, om);
+  weights2_ind64(q, k, w64, w, r, om);
   combine2<float>(k, r, om, w, cu);
 }
 
