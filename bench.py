@@ -47,9 +47,10 @@ ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64",
         ("fp32_ind64_typical", "FP32_IND64", False, {"smoothness": "BETA_TYPICAL"}),
         ("fp32_ind64_component", "FP32_IND64", False, {"charwise": 0})]
 FLOPS_PER_CELL_STAGE = {"fp64": 5712.0, "fp32": 5313.0, "fp32_ind64": None}
+MIXED_FP64_FLOPS_PER_CELL_STAGE = None
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
-                "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); the "
-                "mixed kernel counts its FP64 flops (its bound)")
+                "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); FP64 flops "
+                "for the fp64 arm, FP32 flops for the fp32 and fp32_ind64 arms")
 # DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
 # the bench grid by cell count; None once the kernel has changed since the capture.
 TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 335.3e6 / 1536 ** 2, "fp32_ind64": None}
@@ -540,6 +541,12 @@ def main():
             achieved = fl * ncells / (r["stage_ms_avg"] * 1e-3) / 1e12
             out.update({"achieved": achieved, "frac": achieved / peak_tf, "flops_per_cell_stage": fl,
                         "flops_source": FLOPS_SOURCE})
+            if key == "fp32_ind64" and MIXED_FP64_FLOPS_PER_CELL_STAGE is not None:
+                # the FP64 indicator work runs only where the FP32 screen cannot
+                # rule it out: data dependent, reported beside the bound
+                f64 = MIXED_FP64_FLOPS_PER_CELL_STAGE
+                out["fp64_flops_per_cell_stage"] = f64
+                out["fp64_frac"] = f64 * ncells / (r["stage_ms_avg"] * 1e-3) / 1e12 / fp64_peak
         else:
             out.update({"achieved": None, "frac": None, "flops_per_cell_stage": None,
                         "flops_source": "not yet counted for this kernel"})
@@ -556,7 +563,7 @@ def main():
         v = world * ncells * 3 * args.steps / (r["ms"] * 1e-3)
         out = {"value": v, "ms_per_step": r["ms"] / args.steps,
                "dtype": {hw.FP64: "f64", hw.FP32: "f32", hw.FP32_IND64: "f32 (f64 indicators/weights)"}[prec],
-               "roofline": roofline(r, prec, fp32_peak if prec == hw.FP32 else fp64_peak,
+               "roofline": roofline(r, prec, fp64_peak if prec == hw.FP64 else fp32_peak,
                                     learned=r["smooth_fraction"] is not None),
                "hbm": hbm(r, 8 if prec == hw.FP64 else 4), "clocks": r["clocks"], "gpu_launches": r["launches"],
                "launch_shape": r["launch_shape"]}
@@ -588,8 +595,9 @@ def main():
                        "l2": "inputs larger than L2 (state 1.6 GB FP64, 0.8 GB FP32 at 4096^2)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": hs["roofline"],
-            "roofline_note": "bound 'alu': FP64 pipe for the fp64 and fp32_ind64 arms, FP32 FMA pipe for fp32; "
-                             "peaks from the FMA probe on this GPU (recipe nominal FP64 1.25 TFLOP/s)",
+            "roofline_note": "bound 'alu': FP64 pipe for the fp64 arm; FP32 FMA pipe for fp32 and fp32_ind64 (its "
+                             "FP64 indicator runs only where an FP32 screen cannot rule it out: fp64_frac, counted "
+                             "at 1536^2); peaks from the FMA probe on this GPU (recipe nominal FP64 1.25 TFLOP/s)",
             "hbm": hs["hbm"],
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -348,7 +348,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
 // run-time switches).  BATCH: the tiles of many 2D instances of uneven sizes
 // (a tile table; per-instance descriptors and control blocks).
 template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
-__global__ void __launch_bounds__(kThreads2, (sizeof(T) == 4 && !W64) ? 2 : 1) k_stage2d(const Stage2Args a) {
+__global__ void __launch_bounds__(kThreads2, sizeof(T) == 4 ? 2 : 1) k_stage2d(const Stage2Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   constexpr int NF = 3 * NC;
   extern __shared__ __align__(16) unsigned char hw_smem[];
