@@ -46,14 +46,14 @@ ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64",
         ("fp32_learned", "FP32", True, {}), ("fp32_ind64_learned", "FP32_IND64", True, {}),
         ("fp32_ind64_typical", "FP32_IND64", False, {"smoothness": "BETA_TYPICAL"}),
         ("fp32_ind64_component", "FP32_IND64", False, {"charwise": 0})]
-FLOPS_PER_CELL_STAGE = {"fp64": 5712.0, "fp32": 5313.0, "fp32_ind64": None}
-MIXED_FP64_FLOPS_PER_CELL_STAGE = None
+FLOPS_PER_CELL_STAGE = {"fp64": 5712.0, "fp32": 5313.0, "fp32_ind64": 5915.0}
+MIXED_FP64_FLOPS_PER_CELL_STAGE = 29.5  # early-time 1536^2 state; data dependent
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
                 "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); FP64 flops "
                 "for the fp64 arm, FP32 flops for the fp32 and fp32_ind64 arms")
 # DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
 # the bench grid by cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 335.3e6 / 1536 ** 2, "fp32_ind64": None}
+TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 335.3e6 / 1536 ** 2, "fp32_ind64": 364.5e6 / 1536 ** 2}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 1536^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)
@@ -387,6 +387,52 @@ def run_batch2d(args, hw, torch, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_single_grid(args, hw, torch, rank, local, workload, cfg_kw, U0, arms, flush_l2):
+    """Time `arms` [(name, precision)] of one grid from U0 (each step timed
+    alone after an optional 256 MB L2 flush); one JSON line, headline the
+    last arm."""
+    torch.cuda.set_device(local)
+    U0 = torch.from_numpy(U0)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_l2 else None
+    cells = int(np.prod(U0.shape[1:]))
+    out = {}
+    for name, prec in arms:
+        s = hw.Solver(hw.Config(precision=prec, **cfg_kw))
+        s.set_state(U0.cuda())
+        hw.hweno_autotune(s.h, reps=2)
+        s.advance(1e30, max_steps=args.warmup)
+        s.set_state(U0.cuda())
+        stream = torch.cuda.ExternalStream(s.stream)
+        total_ms = 0.0
+        steps_left = args.steps
+        while steps_left > 0:
+            k = 1 if flush_l2 else steps_left
+            if flush_l2:
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.advance(1e30, max_steps=k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            steps_left -= k
+        out[name] = {"value": cells * 3 * args.steps / (total_ms * 1e-3), "ms_per_step": total_ms / args.steps}
+        s.close()
+    head = arms[-1][0]
+    if rank == 0:
+        line = {"metric": METRIC, "value": out[head]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out[head]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": {"FP64": "f64", "FP32": "f32"}.get(
+                    head.upper(), "f32 (f64 indicators/weights)"),
+                "data": "synthetic (closed-form initial data)",
+                "config": {"workload": workload, "cells": cells,
+                           "l2": "flushed (256 MB write) before every timed step" if flush_l2
+                           else "inputs larger than L2"},
+                "arms": out}
+        print(json.dumps(line), flush=True)
+
+
 def run_dmr(args, hw, torch, rank, local):
     """The double Mach reflection on the paper's 1920 x 480 mesh (split
     reflective wall, moving-shock top boundary), from its initial state:
@@ -447,11 +493,13 @@ def main():
     ap.add_argument("--only", choices=[a[0] for a in ARMS], default=None,
                     help="time one arm only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["euler2d_quadrant", "batch1d", "batch2d", "dmr"],
+    ap.add_argument("--workload", choices=["euler2d_quadrant", "batch1d", "batch2d", "dmr", "advection1d",
+                                           "burgers2d"],
                     default="euler2d_quadrant",
                     help="batch1d: 256 seeded 1D Euler Riemann problems of uneven sizes in one batch; "
                          "batch2d: 48 seeded 2D four-quadrant problems of uneven sizes in one batch; "
-                         "dmr: the double Mach reflection on the paper's 1920 x 480 mesh")
+                         "dmr: the double Mach reflection on the paper's 1920 x 480 mesh; "
+                         "advection1d / burgers2d: the throughput runs of Examples 1 and 3")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -471,6 +519,23 @@ def main():
         return
     if args.workload == "batch2d":
         run_batch2d(args, hw, torch, rank, local)
+        return
+    if args.workload == "advection1d":
+        from paper_2607_24325_b300 import workloads as W
+        n = 1 << 24
+        run_single_grid(args, hw, torch, rank, local,
+                        "1D linear advection u0 = sin(pi x) on [0,2], periodic, 2^24 cells",
+                        dict(dim=1, nx=n, xlo=0.0, xhi=2.0, equation=hw.EQ_ADVECTION, adv_x=1.0),
+                        W.sine_1d_cells(n), [("fp32", hw.FP32), ("fp64", hw.FP64)], flush_l2=False)
+        return
+    if args.workload == "burgers2d":
+        from paper_2607_24325_b300 import workloads as W
+        n = 4096
+        run_single_grid(args, hw, torch, rank, local,
+                        "2D Burgers u0 = 0.5 + sin(pi (x + y) / 2) on [0,4]^2, periodic, 4096^2 cells",
+                        dict(dim=2, nx=n, ny=n, xlo=0.0, xhi=4.0, ylo=0.0, yhi=4.0, equation=hw.EQ_BURGERS,
+                             lin_w=W2D), W.sine_2d_cells(n, n),
+                        [("fp32", hw.FP32), ("fp32_ind64", hw.FP32_IND64), ("fp64", hw.FP64)], flush_l2=False)
         return
 
     torch.cuda.set_device(local)

@@ -397,3 +397,37 @@ def quadrant_batch_2d(n: int = 48, seed: int = 2025, nmin: int = 96, nmax: int =
     states = [quadrant_2d(quadrant_states(seed + k), split[k, 0], split[k, 1], 0.0, 1.0, 0.0, 1.0, *sizes[k])
               for k in range(n)]
     return sizes, states
+
+
+# --------------------------------------------------------------------------
+# Closed-form cell data of sine waves at large sizes (the throughput runs of
+# Examples 1 and 3): the cell mean of sin(k s) over [s - h/2, s + h/2] is
+# sin(k s) sin(k h / 2) / (k h / 2).
+# --------------------------------------------------------------------------
+def _sinc_half(k, h):
+    z = 0.5 * k * h
+    return math.sin(z) / z
+
+
+def sine_1d_cells(n: int, xlo: float = 0.0, xhi: float = 2.0, k: float = math.pi, offset: float = 0.0):
+    """u0 = offset + sin(k x): exact cell averages and v-bar (the mean of u_x,
+    i.e. the face difference over dx), [2, n]."""
+    dx = (xhi - xlo) / n
+    xc = xlo + (np.arange(n) + 0.5) * dx
+    ubar = offset + np.sin(k * xc) * _sinc_half(k, dx)
+    vbar = (np.sin(k * (xc + 0.5 * dx)) - np.sin(k * (xc - 0.5 * dx))) / dx
+    return np.stack([ubar, vbar])
+
+
+def sine_2d_cells(nx: int, ny: int, xlo: float = 0.0, xhi: float = 4.0, ylo: float = 0.0, yhi: float = 4.0,
+                  k: float = 0.5 * math.pi, offset: float = 0.5):
+    """u0 = offset + sin(k (x + y)) (Example 3 with offset 0.5 and k = pi/2):
+    exact cell averages and scaled moments, [3, ny, nx]."""
+    dx, dy = (xhi - xlo) / nx, (yhi - ylo) / ny
+    xc = (xlo + (np.arange(nx) + 0.5) * dx)[None, :]
+    yc = (ylo + (np.arange(ny) + 0.5) * dy)[:, None]
+    sx, sy = _sinc_half(k, dx), _sinc_half(k, dy)
+    ubar = offset + np.sin(k * (xc + yc)) * sx * sy
+    vbar = (np.sin(k * (xc + 0.5 * dx + yc)) - np.sin(k * (xc - 0.5 * dx + yc))) * sy
+    wbar = (np.sin(k * (xc + yc + 0.5 * dy)) - np.sin(k * (xc + yc - 0.5 * dy))) * sx
+    return np.stack([ubar, vbar, wbar])
