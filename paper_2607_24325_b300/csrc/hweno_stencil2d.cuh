@@ -275,15 +275,18 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
   // FP32 screen: a sound upper bound on every a_m = tau^2 / (beta_m^p + eps)
   // from the FP32 coefficients k.  Each c~_l combines the stencil differences
   // and moments (largest magnitude S) and errs by at most ~30 u S in FP32
-  // (u = 2^-24), bounded here by E = 2^-16 S; hence
-  //   |beta~_0 - beta_0| <= 2^-19 beta~_0 + E (2 sum_l w_l |c~_l| + 1331 E),
+  // (u = 2^-24), bounded here by E = 2^-16 S.  beta_0 is a quadratic form
+  // sum_t m_t c_a c_b with positive m_t (the moment form: squares only; the
+  // Jiang-Shu form: 29 terms), so
+  //   |beta~_0 - beta_0| <= 2^-18 A + E (G + E sum_t m_t),
+  // A the form at |c~|, G = sum_l R_l |c~_l| with R_l the form's row sums;
   //   |beta~_m - beta_m| <= 2^-20 beta~_m  (m >= 1),
   // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  Where the
   // bound puts every a_m below 2^-28 for all 32 lanes, 1 + a_m is 1 in FP32
   // whatever the FP64 evaluation gives, so that evaluation is skipped and
   // the result is the same bit for bit.
-  bool quiet = !w.typical;  // the bound is written for the moment form
-  if (quiet) {
+  bool quiet = true;
+  {
     float S = 0.0f;
 #pragma unroll
     for (int s = 0; s < 9; ++s)
@@ -291,21 +294,32 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
 #pragma unroll
     for (int s = 9; s < 17; ++s) S = fmaxf(S, fabsf(q[s]));
     const float* c = k.c;
-    const float sw = (fabsf(c[1]) + fabsf(c[2]) + fabsf(c[4])) +
-                     4.0f * (fabsf(c[3]) + fabsf(c[5]) + fabsf(c[7]) + fabsf(c[8])) +
-                     36.0f * (fabsf(c[6]) + fabsf(c[9]) + fabsf(c[11]) + fabsf(c[13])) +
-                     576.0f * (fabsf(c[10]) + fabsf(c[14])) + 16.0f * fabsf(c[12]);
-    float bs[5];
-    bs[0] = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] + 4.0f * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
-            36.0f * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
-            576.0f * (c[10] * c[10] + c[14] * c[14]) + 16.0f * c[12] * c[12];
+    float ac[15];
+#pragma unroll
+    for (int l = 0; l < 15; ++l) ac[l] = fabsf(c[l]);
+    const float E = S * 0x1p-16f;
+    float bs[5], Ds[5];
+    if (w.typical) {
+      bs[0] = beta_typical_2d(c);
+      const float A = beta_typical_2d(ac);
+      const float G = 2.667f * (ac[1] + ac[2]) + 13.59f * (ac[3] + ac[5]) + 3.467f * ac[4] +
+                      78.77f * (ac[6] + ac[9]) + 9.623f * (ac[7] + ac[8]) + 1256.3f * (ac[10] + ac[14]) +
+                      85.46f * (ac[11] + ac[13]) + 39.92f * ac[12];
+      Ds[0] = 0x1p-18f * A + E * (G + 1469.0f * E);
+    } else {
+      bs[0] = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
+              4.0f * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
+              36.0f * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
+              576.0f * (c[10] * c[10] + c[14] * c[14]) + 16.0f * c[12] * c[12];
+      const float G = 2.0f * ((ac[1] + ac[2] + ac[4]) + 4.0f * (ac[3] + ac[5] + ac[7] + ac[8]) +
+                              36.0f * (ac[6] + ac[9] + ac[11] + ac[13]) + 576.0f * (ac[10] + ac[14]) +
+                              16.0f * ac[12]);
+      Ds[0] = 0x1p-18f * bs[0] + E * (G + 1331.0f * E);
+    }
     bs[1] = k.dW * k.dW + k.dS * k.dS;
     bs[2] = k.dE * k.dE + k.dS * k.dS;
     bs[3] = k.dE * k.dE + k.dN * k.dN;
     bs[4] = k.dW * k.dW + k.dN * k.dN;
-    const float E = S * 0x1p-16f;
-    float Ds[5];
-    Ds[0] = 0x1p-19f * bs[0] + E * (2.0f * sw + 1331.0f * E);
 #pragma unroll
     for (int m = 1; m < 5; ++m) Ds[m] = 0x1p-20f * bs[m];
     const float tau = 0.25f * ((fabsf(bs[0] - bs[1]) + fabsf(bs[0] - bs[2])) +
