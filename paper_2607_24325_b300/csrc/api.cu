@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hweno.h"
 #include "hweno_types.h"
 #include "kernels.h"
@@ -47,6 +49,16 @@ hweno_status fail(hweno_status st, const char* fmt, ...) {
   } while (0)
 
 constexpr int kGraphSteps = 16;
+
+// NVTX range over a scope: the library's phases (state transfer, graph
+// capture and replay, stage launches, indicator, autotuning) show up by name
+// on an Nsight timeline; without an attached tool each call is a no-op.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 hweno_status validate(const hweno_config* c, int expect_dim) {
   if (!c) return fail(HWENO_ERR_ARG, "config is NULL");
@@ -303,6 +315,8 @@ struct Engine {
 
   hweno_status stage(int s, const void* in, void* out, hw::Ctl* c, double ax, double ay,
                      void* hat) {
+    static const char* kNames[4] = {"hweno.operator", "hweno.stage1", "hweno.stage2", "hweno.stage3"};
+    Range r(kNames[s]);
     if (dim == 1) {
       hw::Stage1Args a{};
       a.in = in; a.base = S; a.out = out; a.hat = hat;
@@ -351,6 +365,7 @@ struct Engine {
   }
 
   hweno_status run_indicator() {
+    Range r("hweno.indicator");
     hw::MlpDev m{mlp_w, mlp_w + 32 * 80, mlp_bias, z_thresh};
     HW_CK(hw::launch_mlp_infer2d(prec, cfg.equation, S, grid, cells, m, ctl, troubled, smooth, num_sms, own));
     return HWENO_OK;
@@ -405,6 +420,7 @@ struct Engine {
   }
 
   hweno_status set_state(const void* U, int on_device) {
+    Range r("hweno.set_state");
     if (!U) return fail(HWENO_ERR_ARG, "state pointer is NULL");
     HW_TRY(enter());
     HW_CK(cudaStreamSynchronize(own));
@@ -420,6 +436,7 @@ struct Engine {
   }
 
   hweno_status get_state(void* U, int on_device) {
+    Range r("hweno.get_state");
     if (!U) return fail(HWENO_ERR_ARG, "state pointer is NULL");
     if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
     HW_TRY(enter());
@@ -436,6 +453,7 @@ struct Engine {
   }
 
   hweno_status build_graph() {
+    Range r("hweno.capture");
     if (gexec) return HWENO_OK;
     cudaGraph_t g = nullptr;
     HW_CK(cudaStreamBeginCapture(own, cudaStreamCaptureModeThreadLocal));
@@ -454,6 +472,7 @@ struct Engine {
   }
 
   hweno_status advance(const double* t_final, int max_steps) {
+    Range r("hweno.advance");
     if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
     if (max_steps < 0) return fail(HWENO_ERR_ARG, "max_steps must be >= 0");
     for (int k = 0; k < n_inst; ++k)
@@ -475,6 +494,7 @@ struct Engine {
     while (remaining > 0) {
       const int chunk = remaining >= kGraphSteps ? kGraphSteps : (int)remaining;
       if (chunk == kGraphSteps && !prof) {
+        Range g("hweno.graph16");
         HW_CK(cudaGraphLaunch(gexec, own));
       } else {
         for (int s = 0; s < chunk; ++s) HW_TRY(one_step());
@@ -575,6 +595,7 @@ struct Engine {
   // Time every candidate launch shape on the current state (operator mode,
   // reps launches each, CUDA events) and keep the fastest.
   hweno_status autotune(int reps, double* best_ms) {
+    Range r("hweno.autotune");
     if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
     if (reps < 1 || reps > 1000) return fail(HWENO_ERR_ARG, "reps must lie in [1, 1000]");
     HW_TRY(enter());
