@@ -68,6 +68,25 @@ __device__ __forceinline__ float rcp_approx(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// The value itself, hidden from the optimiser: an expression that produced
+// it is rounded to a register value and never fused into its readers
+// (so every reader, in any code context, sees the same bits).
+__device__ __forceinline__ float opaque(float x) {
+  asm("" : "+f"(x));
+  return x;
+}
+__device__ __forceinline__ double opaque(double x) {
+  asm("" : "+d"(x));
+  return x;
+}
+
+// Square root to within a few units of 2^-23 relative (PTX sqrt.approx,
+// subnormal inputs kept): for bounds that carry their own margin.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp_t(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double div_t(double a, double b) { return a / b; }

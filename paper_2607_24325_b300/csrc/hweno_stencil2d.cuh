@@ -12,21 +12,58 @@ namespace hw {
 constexpr int kT2 = 30;           // interior tile edge
 constexpr int kBox = 34;          // tile + 2 halo cells per side
 constexpr int kBP = 35;           // box pitch (odd: conflict-free column walks)
-constexpr int kFS = kBox * kBP;   // box field stride
-constexpr int kSP = 30;           // stash pitch
-constexpr int kSS = kT2 * kSP + 4;  // stash field stride (room for the row skew)
+constexpr int kFS = kBox * kBP;   // box group stride, in cells
+constexpr int kSP = 30;           // stash pitch, in cells
+constexpr int kSS = kT2 * kSP + 8;  // stash quantity stride, in cells (room for the row skew)
+// Threads per stage-kernel CTA (two CTAs per SM in FP32, one in FP64).
+// The tile's 30 rows per pass are dealt to the warps in turn.
+template <typename T, bool W64>
+constexpr int threads2() { return W64 ? 256 : 256; }
 
-// Stash offset of tile cell (row r, column c).  The x pass writes rows
-// (consecutive lanes, consecutive words); the y pass reads columns (lane =
-// row, stride kSP).  A stride of 30 words alone would pair lanes l and l+16
-// (FP32) or l and l+8 (FP64, two banks per element) on one bank; skewing
-// every 16th (FP32) or 8th (FP64) row by one element keeps both walks
-// conflict-free.
-template <typename T>
-__device__ __forceinline__ int stash_at(int r, int c) {
-  return r * kSP + c + (r >> (sizeof(T) == 8 ? 3 : 4));
+// The NC components of one cell as vector loads / stores (16-byte accesses
+// for the four Euler components; the address must be 16-byte aligned).
+template <typename T, int NC>
+__device__ __forceinline__ void vec_load(const T* __restrict__ p, T* x) {
+  if constexpr (NC == 4) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(p);
+      const double2 b = *reinterpret_cast<const double2*>(p + 2);
+      x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+  } else {
+    x[0] = p[0];
+  }
 }
-constexpr int kThreads2 = 256;
+template <typename T, int NC>
+__device__ __forceinline__ void vec_store(T* p, const T* x) {
+  if constexpr (NC == 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    } else {
+      *reinterpret_cast<double2*>(p) = make_double2(x[0], x[1]);
+      *reinterpret_cast<double2*>(p + 2) = make_double2(x[2], x[3]);
+    }
+  } else {
+    p[0] = x[0];
+  }
+}
+
+// The stash holds the x pass's results per tile cell: quantity q (L_u,
+// L_v, L_w, v-hat), then the cell, then its NC components.  The x pass
+// writes rows (consecutive lanes, consecutive cells); the y pass reads
+// columns (lane = row, stride kSP cells).  A stride of 30 cells alone puts
+// lanes 4 rows apart (16-byte cells: 8 to a 128-byte line) or 16 rows apart
+// (4-byte cells) on one bank; skewing the rows by one cell every 4 (16 and
+// 32-byte cells), 8 (8-byte) or 16 (4-byte) rows spreads a column walk
+// over the banks.
+template <typename T, int NC>
+__device__ __forceinline__ int stash_at(int q, int r, int c) {
+  constexpr int sh = NC == 4 ? 2 : (sizeof(T) == 8 ? 3 : 4);
+  return (q * kSS + r * kSP + c + (r >> sh)) * NC;
+}
 
 template <int NC>
 constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
@@ -34,6 +71,27 @@ constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
 template <typename T, int NC>
 constexpr size_t smem_bytes2() {
   return sizeof(T) * (size_t)(3 * NC * kFS + stash_fields<NC>() * kSS);
+}
+
+// The halo box is cell-interleaved: group d (0 averages, 1 x-moments,
+// 2 y-moments), then the cell (row * kBP + column), then the NC components,
+// so the four Euler components of one stencil value are one 16-byte (FP32)
+// or two 16-byte (FP64) shared-memory loads.
+template <int NC>
+__device__ __forceinline__ int box_at(int d, int cell, int k) {
+  return (d * kFS + cell) * NC + k;
+}
+
+// The NC components of group d at a box cell, in pass-frame order (the y
+// pass swaps the momentum components).
+template <typename T, int NC>
+__device__ __forceinline__ void box_load(const T* __restrict__ box, int d, int cell, int D, T* x) {
+  vec_load<T, NC>(box + box_at<NC>(d, cell, 0), x);
+  if constexpr (NC == 4) {
+    const T a = x[1], b = x[2];
+    x[1] = D == 0 ? a : b;
+    x[2] = D == 0 ? b : a;
+  }
 }
 
 // Component of the pass frame holding physical component k (an involution).
@@ -68,13 +126,6 @@ __device__ __forceinline__ SideRule side_rule(const Grid2& G, int sd, double lo,
     }
   }
   return r;
-}
-
-// frame_field with the direction known only at run time (the compiler folds
-// the component and field constants; D selects between two of them).
-template <int EQ, int NC>
-__device__ __forceinline__ int frame_field_rt(int D, int d, int k) {
-  return D == 0 ? frame_field<0, EQ, NC>(d, k) : frame_field<1, EQ, NC>(d, k);
 }
 
 // Value of field f at cell (i, j), ghost cells resolved as "x sides for the
@@ -243,9 +294,14 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
   combine2<T>(k, r, om, w, cu);
 }
 
-// Mixed precision, Steps 2-3 for one field: FP64 smoothness indicators and
-// nonlinear weights of the FP32 stencil values q, returned narrowed to FP32
-// (r = omega_0 / gamma_0, om[1..4]).
+// The stencil values of one field, by value (the argument of the FP64
+// indicator below).
+struct Stencil17 { float q[17]; };
+struct Weights5 { float a[5]; };
+
+// Mixed precision, the FP64 part of Steps 2-3 for one field: a_m =
+// tau^2 / (beta_m^{1|2} + eps) from the FP32 stencil values q, rounded to
+// FP32.
 //  * The indicator uses c_1..c_14 only, each c_l = u_l / den_l with u_l an
 //    integer-weighted sum of the centre-shifted averages and the moments;
 //    the 1/den_l^2 factors are folded into beta_0's weights (m! n!)^2:
@@ -255,12 +311,12 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
 //  * The inputs are widened exactly on the integer ALU; the differences
 //    q_k - q5 are taken in FP32 when that is exact for all 32 lanes (checked
 //    with Knuth's TwoSum error term), else in FP64.
-//  * beta_m, tau and a_m = tau^2 / (beta_m + eps) in FP64 (the reciprocal by
-//    rcp_newton); a_m rounded to FP32 and the normalisation of
-//    w~_m = gamma_m (1 + a_m) in FP32: every term is positive, so it adds
-//    no more than a few FP32 ulp to the weights, which are FP32 anyway.
-__device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
-                                               const WeightsT<float>& wf, float& r, float* om) {
+//  * beta_m, tau and a_m in FP64 (the reciprocal by rcp_newton).
+// Not inlined: it runs only for warps the FP32 screen cannot clear, and as a
+// call its register demand is met by saves on that path alone instead of
+// spills of the caller's live values on every path.  All 32 lanes call it.
+static __device__ __noinline__ Weights5 indicator64(const Stencil17 st, double eps, int pow2, int typical) {
+  const float* q = st.q;
   const float q5f = q[4];
   float d32[9];
   bool exact = true;
@@ -272,6 +328,71 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
     exact = exact && ((a - (sum - bb)) + (b - bb)) == 0.0f;
     d32[s] = sum;
   }
+  Weights5 out;
+  float* a = out.a;
+  double d[9];
+  if (__all_sync(HW_FULL_MASK, exact)) {
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+      if (s != 4) d[s] = widen_f32(d32[s]);
+  } else {
+    const double q5 = widen_f32(q5f);
+#pragma unroll
+    for (int s = 0; s < 9; ++s)
+      if (s != 4) d[s] = widen_f32(q[s]) - q5;
+  }
+  const double d1 = d[0], d2 = d[1], d3 = d[2], d4 = d[3], d6 = d[5], d7 = d[6], d8 = d[7], d9 = d[8];
+  const double q10 = widen_f32(q[9]), q11 = widen_f32(q[10]), q12 = widen_f32(q[11]), q13 = widen_f32(q[12]);
+  const double q14 = widen_f32(q[13]), q15 = widen_f32(q[14]), q16 = widen_f32(q[15]), q17 = widen_f32(q[16]);
+  const double s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
+  const double sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
+  const double ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
+  const double s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
+  const double s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
+  const double u1 = 2.0 * ax + 19.0 * dxe - 6.0 * s1011 + 3.0 * s1213;
+  const double u2 = 2.0 * ay + 19.0 * dye + 3.0 * s1415 - 6.0 * s1617;
+  const double u3 = 2.0 * ey - sc + 62.0 * ex - 18.0 * m1110;
+  const double u5 = 2.0 * ex - sc + 62.0 * ey - 18.0 * m1716;
+  const double u4 = 3.0 * cx + 5.0 * (m1213 + m1415);
+  const double u6 = 4.0 * (s1011 - dxe) - ax - 2.0 * s1213;
+  const double u9 = 4.0 * (s1617 - dye) - ay - 2.0 * s1415;
+  const double u7 = ay + 2.0 * dye, u8 = ax + 2.0 * dxe;
+  const double u10 = m1110 - 2.0 * ex, u14 = m1716 - 2.0 * ey;
+  const double u11 = cx + 2.0 * m1213, u13 = cx + 2.0 * m1415;
+  const double u12 = sc - 2.0 * (ex + ey);
+  double b0;
+  if (typical) {  // the Jiang-Shu form needs the scaled coefficients c_l = u_l / den_l
+    const double c[15] = {0.0,         u1 * (1.0 / 24.0), u2 * (1.0 / 24.0), u3 * (1.0 / 48.0), -0.125 * u4,
+                          u5 * (1.0 / 48.0), 0.05 * u6,   -0.25 * u7,        -0.25 * u8,        0.05 * u9,
+                          0.25 * u10,  0.25 * u11,        0.25 * u12,        0.25 * u13,        0.25 * u14};
+    b0 = beta_typical_2d(c);
+  } else {
+    double acc = u1 * u1 + u2 * u2 + u3 * u3 + u5 * u5 + 9.0 * u4 * u4;
+    acc += 144.0 * (u7 * u7 + u8 * u8) + 51.84 * (u6 * u6 + u9 * u9);
+    acc += 1296.0 * (u11 * u11 + u13 * u13) + 20736.0 * (u10 * u10 + u14 * u14) + 576.0 * u12 * u12;
+    b0 = acc * (1.0 / 576.0);
+  }
+  const double w2 = d4 * d4, e2 = d6 * d6, s2 = d2 * d2, n2 = d8 * d8;  // dW, dE, dS, dN squared
+  const double b1 = w2 + s2, b2 = e2 + s2, b3 = e2 + n2, b4 = w2 + n2;
+  const double tau = 0.25 * ((fabs(b0 - b1) + fabs(b0 - b2)) + (fabs(b0 - b3) + fabs(b0 - b4)));
+  // the epsilon-sensitive part in FP64: a_m = tau^2 / (beta_m^{1|2} + eps)
+  const double t2 = tau * tau;
+  const double beta[5] = {b0, b1, b2, b3, b4};
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const double dm = (pow2 ? beta[m] * beta[m] : beta[m]) + eps;
+    a[m] = narrow_f64_ftz(t2 * rcp_newton(dm));
+  }
+  return out;
+}
+
+// Mixed precision, Steps 2-3 for one field, FP32 part: the screen.  True
+// where every a_m = tau^2 / (beta_m^p + eps) is provably below 2^-28, so
+// that 1 + a_m is 1 in FP32 and a_m = 0 gives the FP64 evaluation's result
+// bit for bit.
+__device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
+                                        const WeightsT<float>& wf) {
+  const float q5f = q[4];
   // FP32 screen: a sound upper bound on every a_m = tau^2 / (beta_m^p + eps)
   // from the FP32 coefficients k.  Each c~_l combines the stencil differences
   // and moments (largest magnitude S) and errs by at most ~30 u S in FP32
@@ -281,25 +402,28 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
   //   |beta~_0 - beta_0| <= 2^-18 A + E (G + E sum_t m_t),
   // A the form at |c~|, G = sum_l R_l |c~_l| with R_l the form's row sums;
   //   |beta~_m - beta_m| <= 2^-20 beta~_m  (m >= 1),
-  // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  Where the
-  // bound puts every a_m below 2^-28 for all 32 lanes, 1 + a_m is 1 in FP32
-  // whatever the FP64 evaluation gives, so that evaluation is skipped and
-  // the result is the same bit for bit.
-  bool quiet = true;
+  // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  For the
+  // moment form (weights w_l summing to 1331) Cauchy-Schwarz gives
+  // G = 2 sum_l w_l |c~_l| <= 2 sqrt(1331 A) <= 72.97 sqrt(beta~_0), taken
+  // as 73 sqrt(beta~_0).  Where the bound puts every a_m below 2^-28 for
+  // all 32 lanes, 1 + a_m is 1 in FP32 whatever the FP64 evaluation gives,
+  // so that evaluation is skipped and the result is the same bit for bit
+  // (any sound bound keeps this; a looser one only skips less often).
+  bool quiet;
   {
     float S = 0.0f;
 #pragma unroll
     for (int s = 0; s < 9; ++s)
-      if (s != 4) S = fmaxf(S, fabsf(d32[s]));
+      if (s != 4) S = fmaxf(S, fabsf(q[s] - q5f));
 #pragma unroll
     for (int s = 9; s < 17; ++s) S = fmaxf(S, fabsf(q[s]));
     const float* c = k.c;
-    float ac[15];
-#pragma unroll
-    for (int l = 0; l < 15; ++l) ac[l] = fabsf(c[l]);
     const float E = S * 0x1p-16f;
     float bs[5], Ds[5];
     if (w.typical) {
+      float ac[15];
+#pragma unroll
+      for (int l = 0; l < 15; ++l) ac[l] = fabsf(c[l]);
       bs[0] = beta_typical_2d(c);
       const float A = beta_typical_2d(ac);
       const float G = 2.667f * (ac[1] + ac[2]) + 13.59f * (ac[3] + ac[5]) + 3.467f * ac[4] +
@@ -311,9 +435,7 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
               4.0f * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
               36.0f * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
               576.0f * (c[10] * c[10] + c[14] * c[14]) + 16.0f * c[12] * c[12];
-      const float G = 2.0f * ((ac[1] + ac[2] + ac[4]) + 4.0f * (ac[3] + ac[5] + ac[7] + ac[8]) +
-                              36.0f * (ac[6] + ac[9] + ac[11] + ac[13]) + 576.0f * (ac[10] + ac[14]) +
-                              16.0f * ac[12]);
+      const float G = 73.0f * sqrt_approx(bs[0]);
       Ds[0] = 0x1p-18f * bs[0] + E * (G + 1331.0f * E);
     }
     bs[1] = k.dW * k.dW + k.dS * k.dS;
@@ -326,74 +448,22 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
                                (fabsf(bs[0] - bs[3]) + fabsf(bs[0] - bs[4])));
     const float ut = tau * (1.0f + 0x1p-20f) + Ds[0] + 0.25f * ((Ds[1] + Ds[2]) + (Ds[3] + Ds[4]));
     const float ut2 = ut * ut;
+    // every a_m small <=> small against the least lower bound of beta_m
+    // (x -> x^p + eps rounds monotonically)
+    float L = bs[0] - Ds[0];
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const float L = fmaxf(bs[m] - Ds[m], 0.0f);
-      const float dlo = (wf.pow2 ? L * L : L) + wf.eps;
-      quiet = quiet && ut2 < 0x1p-28f * dlo;
-    }
+    for (int m = 1; m < 5; ++m) L = fminf(L, bs[m] - Ds[m]);
+    L = fmaxf(L, 0.0f);
+    const float dlo = (wf.pow2 ? L * L : L) + wf.eps;
+    quiet = ut2 < 0x1p-28f * dlo;
   }
-  float a[5];
-  if (__all_sync(HW_FULL_MASK, quiet)) {
-#pragma unroll
-    for (int m = 0; m < 5; ++m) a[m] = 0.0f;
-  } else {
-    double d[9];
-    if (__all_sync(HW_FULL_MASK, exact)) {
-#pragma unroll
-      for (int s = 0; s < 9; ++s)
-        if (s != 4) d[s] = widen_f32(d32[s]);
-    } else {
-      const double q5 = widen_f32(q5f);
-#pragma unroll
-      for (int s = 0; s < 9; ++s)
-        if (s != 4) d[s] = widen_f32(q[s]) - q5;
-    }
-    const double d1 = d[0], d2 = d[1], d3 = d[2], d4 = d[3], d6 = d[5], d7 = d[6], d8 = d[7], d9 = d[8];
-    const double q10 = widen_f32(q[9]), q11 = widen_f32(q[10]), q12 = widen_f32(q[11]), q13 = widen_f32(q[12]);
-    const double q14 = widen_f32(q[13]), q15 = widen_f32(q[14]), q16 = widen_f32(q[15]), q17 = widen_f32(q[16]);
-    const double s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
-    const double sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
-    const double ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
-    const double s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
-    const double s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
-    const double u1 = 2.0 * ax + 19.0 * dxe - 6.0 * s1011 + 3.0 * s1213;
-    const double u2 = 2.0 * ay + 19.0 * dye + 3.0 * s1415 - 6.0 * s1617;
-    const double u3 = 2.0 * ey - sc + 62.0 * ex - 18.0 * m1110;
-    const double u5 = 2.0 * ex - sc + 62.0 * ey - 18.0 * m1716;
-    const double u4 = 3.0 * cx + 5.0 * (m1213 + m1415);
-    const double u6 = 4.0 * (s1011 - dxe) - ax - 2.0 * s1213;
-    const double u9 = 4.0 * (s1617 - dye) - ay - 2.0 * s1415;
-    const double u7 = ay + 2.0 * dye, u8 = ax + 2.0 * dxe;
-    const double u10 = m1110 - 2.0 * ex, u14 = m1716 - 2.0 * ey;
-    const double u11 = cx + 2.0 * m1213, u13 = cx + 2.0 * m1415;
-    const double u12 = sc - 2.0 * (ex + ey);
-    double b0;
-    if (w.typical) {  // the Jiang-Shu form needs the scaled coefficients c_l = u_l / den_l
-      const double c[15] = {0.0,         u1 * (1.0 / 24.0), u2 * (1.0 / 24.0), u3 * (1.0 / 48.0), -0.125 * u4,
-                            u5 * (1.0 / 48.0), 0.05 * u6,   -0.25 * u7,        -0.25 * u8,        0.05 * u9,
-                            0.25 * u10,  0.25 * u11,        0.25 * u12,        0.25 * u13,        0.25 * u14};
-      b0 = beta_typical_2d(c);
-    } else {
-      double acc = u1 * u1 + u2 * u2 + u3 * u3 + u5 * u5 + 9.0 * u4 * u4;
-      acc += 144.0 * (u7 * u7 + u8 * u8) + 51.84 * (u6 * u6 + u9 * u9);
-      acc += 1296.0 * (u11 * u11 + u13 * u13) + 20736.0 * (u10 * u10 + u14 * u14) + 576.0 * u12 * u12;
-      b0 = acc * (1.0 / 576.0);
-    }
-    const double w2 = d4 * d4, e2 = d6 * d6, s2 = d2 * d2, n2 = d8 * d8;  // dW, dE, dS, dN squared
-    const double b1 = w2 + s2, b2 = e2 + s2, b3 = e2 + n2, b4 = w2 + n2;
-    const double tau = 0.25 * ((fabs(b0 - b1) + fabs(b0 - b2)) + (fabs(b0 - b3) + fabs(b0 - b4)));
-    // the epsilon-sensitive part in FP64: a_m = tau^2 / (beta_m^{1|2} + eps)
-    const double t2 = tau * tau;
-    const double beta[5] = {b0, b1, b2, b3, b4};
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const double dm = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
-      a[m] = narrow_f64_ftz(t2 * rcp_newton(dm));
-    }
-  }
-  // w~_m = gamma_m (1 + a_m) and the normalisation (well conditioned: all
-  // terms positive) in FP32
+  return quiet;
+}
+
+// Steps 2-3, the weights from a_m (0 where screened, else indicator64):
+// w~_m = gamma_m (1 + a_m) and the normalisation in FP32 (every term
+// positive: a few FP32 ulp at most), r = omega_0 / gamma_0 and om[1..4].
+__device__ __forceinline__ void finish2(const float* a, const WeightsT<float>& wf, float& r, float* om) {
   float e[5], sum = 0.0f;
 #pragma unroll
   for (int m = 0; m < 5; ++m) {
@@ -404,23 +474,6 @@ __device__ __forceinline__ void weights2_ind64(const float* q, const Coef2<float
   r = (1.0f + a[0]) * inv;
 #pragma unroll
   for (int m = 1; m <= 4; ++m) om[m] = e[m] * inv;
-}
-
-// Mixed precision: FP32 inputs and polynomial, the smoothness indicators and
-// nonlinear weights in FP64 (their epsilon-sensitive differences are where
-// FP32 cancels): weights2_ind64.
-__device__ __forceinline__ void recon2_w64(const float* q, const WeightsT<float>& w, const WeightsT<double>& w64,
-                                           bool lin, float* cu) {
-  Coef2<float> k;
-  coef2<float, float>(q, k);
-  if (lin) {  // linear weights: no indicator, plain FP32 coefficients
-#pragma unroll
-    for (int l = 0; l < 15; ++l) cu[l] = k.c[l];
-    return;
-  }
-  float r, om[5];
-  weights2_ind64(q, k, w64, w, r, om);
-  combine2<float>(k, r, om, w, cu);
 }
 
 // Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)

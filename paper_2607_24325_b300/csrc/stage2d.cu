@@ -51,28 +51,152 @@ __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, 
   }
 }
 
+// Stencil value s of the cell at box index cell, in pass-frame components
+// and projected on the characteristic fields of e when chr: s = 0..8 the
+// 3 x 3 cell averages (row-major along the pass normal), 9..12 the moments
+// along the pass normal and 13..16 those along the tangent of the four face
+// neighbours (normal -, +, tangent -, +).
+template <typename T, int NC, bool CHR>
+__device__ __forceinline__ void stencil_at(const T* __restrict__ box, int cell, int D, int s, const Eig<T>& e,
+                                           bool chr, T* x) {
+  const int SN = D == 0 ? 1 : kBP;
+  const int ST = D == 0 ? kBP : 1;
+  const int o9[9] = {-SN - ST, -ST, SN - ST, -SN, 0, SN, -SN + ST, ST, SN + ST};
+  const int o4[4] = {-SN, SN, -ST, ST};
+  const int dd = s < 9 ? 0 : (s < 13 ? 1 : 2);
+  const int off = s < 9 ? o9[s] : o4[(s - 9) & 3];
+  // moment group along the pass normal (dd = 1) or tangent (dd = 2)
+  const int grp = dd == 0 ? 0 : (D == 0 ? dd : 3 - dd);
+  box_load<T, NC>(box, grp, cell + off, D, x);
+  if constexpr (CHR) {
+    if (chr) {
+      T y[4];
+      l2_apply<0>(e, x, y);
+      // materialised: every reader sees the same rounded values
+#pragma unroll
+      for (int k = 0; k < NC; ++k) x[k] = opaque(y[k]);
+    }
+  }
+}
+
+// Position of the n-th (from 0) set bit of m; n < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  int pos = 0;
+#pragma unroll
+  for (int h = 16; h > 0; h >>= 1) {
+    const int c = __popc(m & ((1u << h) - 1u));
+    if (n >= c) {
+      n -= c;
+      m >>= h;
+      pos += h;
+    }
+  }
+  return pos;
+}
+
+// Mixed precision, a deferred warp row: the fields whose FP32 screen did
+// not clear every lane (bit k of pend, warp-uniform; bit k of nqb: this
+// lane's cell not cleared for field k).  Only the uncleared (lane, field)
+// items need the FP64 indicator, so they are packed 32 to a call of
+// indicator64 -- the FP64 pipe runs at 1/64 of the FP32 rate, and a warp
+// instruction costs it the same with 1 or 32 lanes active.  Lane j of a
+// call rebuilds item j's stencil from the box (the owner's cell and
+// eigenvectors) and each owner collects its a_m by shuffle into a[k][m]
+// (0 on cleared lanes: the screen shows 1 + a_m = 1 there).  Runs between
+// rows, when little else is live.
+template <int NC, bool CHR>
+__device__ __forceinline__ void pack64(const float* __restrict__ box, int bidx, int D, bool chr, float g,
+                                       unsigned pend, unsigned nqb, const WeightsT<double>& w64,
+                                       volatile float (*a)[5]) {
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int SL = D == 0 ? 1 : kBP;  // box step between neighbouring lanes' cells
+  unsigned bal[NC];
+  int pre[NC + 1];
+  pre[0] = 0;
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    bal[k] = ((pend >> k) & 1u) ? __ballot_sync(HW_FULL_MASK, (nqb >> k) & 1u) : 0u;
+    pre[k + 1] = pre[k] + __popc(bal[k]);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) a[k][m] = 0.0f;
+  }
+  const int n = pre[NC];
+#pragma unroll 1
+  for (int base = 0; base < n; base += 32) {
+    // this lane's item (idle lanes repeat item base): field f, owner L
+    const int j = base + lane < n ? base + lane : base;
+    int f = 0, pf = 0;
+    unsigned mk = bal[0];
+#pragma unroll
+    for (int k = 1; k < NC; ++k) {
+      if (j >= pre[k]) {
+        f = k;
+        pf = pre[k];
+        mk = bal[k];
+      }
+    }
+    const int L = nth_set_bit(mk, j - pf);
+    const int cell = bidx + (L - lane) * SL;
+    Eig<float> eo{};
+    if constexpr (CHR) {
+      if (chr) {
+        float x0[4];
+        box_load<float, 4>(box, 0, cell, D, x0);
+        eo = eig2<float>(x0[0], x0[1], x0[2], x0[3], g);
+      }
+    }
+    Stencil17 st;
+#pragma unroll
+    for (int s = 0; s < 17; ++s) {
+      float x[NC];
+      stencil_at<float, NC, CHR>(box, cell, D, s, eo, chr, x);
+      float v = x[0];
+#pragma unroll
+      for (int k = 1; k < NC; ++k) v = f == k ? x[k] : v;
+      st.q[s] = v;
+    }
+    const Weights5 r5 = indicator64(st, w64.eps, w64.pow2, w64.typical);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      if ((pend >> k) & 1u) {
+        const int src = pre[k] + __popc(bal[k] & below) - base;
+        const bool mine = ((nqb >> k) & 1u) && src >= 0 && src < 32;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          const float v = __shfl_sync(HW_FULL_MASK, r5.a[m], src & 31);
+          if (mine) a[k][m] = v;
+        }
+      }
+    }
+  }
+}
+
 // One directional pass for the lane's cell at box index bidx.  Returns the
 // Gauss-summed fluxes of the cell's low face (frame components) and the
 // limited derivative along the pass normal.  All 32 lanes must call it.
 // The direction D (0: x pass, 1: y pass on the transposed stencil) is a
 // runtime value: both passes run this one copy of the code, which halves the
 // kernel's instruction footprint (instruction fetch was its top stall).
+//
+// Mixed precision (W64): with redo == 0 the FP32 screen runs per field; a
+// row where it does not clear every lane of some field returns false at
+// once with the fields in *pend and this lane's uncleared ones in *nqb (the
+// caller redoes it after pack64).  With redo != 0 the fields in redo take
+// their a_m from a64.
 template <typename T, int EQ, bool CHR, bool W64>
-__device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, int D, const WeightsT<T>& w,
+__device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int D, const WeightsT<T>& w,
                                        const WeightsT<double>& w64, bool lin, T ihn, T iht, T alpha, T g, T adv,
-                                       T* Fu, T* Fv, T* Fw, T* vh) {
+                                       T* Fu, T* Fv, T* Fw, T* vh, unsigned redo = 0u,
+                                       const volatile float (*a64)[5] = nullptr, unsigned* pend = nullptr,
+                                       unsigned* nqb = nullptr) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
-  const int SN = D == 0 ? 1 : kBP;
-  const int ST = D == 0 ? kBP : 1;
-  const int o9[9] = {-SN - ST, -ST, SN - ST, -SN, 0, SN, -SN + ST, ST, SN + ST};
-  const int o4[4] = {-SN, SN, -ST, ST};
   T cu[NC][15];
   Eig<T> e{};
   const bool chr = CHR && !lin;
   if (chr) {
     T x0[4];
-#pragma unroll
-    for (int k = 0; k < NC; ++k) x0[k] = box[frame_field_rt<EQ, NC>(D, 0, k) * kFS + bidx];
+    box_load<T, 4>(box, 0, bidx, D, x0);
     e = eig2<T>(x0[0], x0[1], x0[2], x0[3], g);
   }
   {
@@ -80,25 +204,46 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, int 
 #pragma unroll
     for (int s = 0; s < 17; ++s) {
       T x[NC];
-      const int dd = s < 9 ? 0 : (s < 13 ? 1 : 2);
-      const int off = s < 9 ? o9[s] : o4[(s - 9) & 3];
-#pragma unroll
-      for (int k = 0; k < NC; ++k) x[k] = box[frame_field_rt<EQ, NC>(D, dd, k) * kFS + bidx + off];
-      if constexpr (CHR) {
-        if (chr) {
-          T y[4];
-          l2_apply<0>(e, x, y);
-#pragma unroll
-          for (int k = 0; k < NC; ++k) x[k] = y[k];
-        }
-      }
+      stencil_at<T, NC, CHR>(box, bidx, D, s, e, chr, x);
 #pragma unroll
       for (int k = 0; k < NC; ++k) q[k][s] = x[k];
     }
+    if constexpr (W64) {
+      // FP32 coefficients and weights; a_m = 0 where the screen clears the
+      // whole warp, from a64 in a redone row
+      unsigned pe = 0u, nb = 0u;
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      if constexpr (W64) recon2_w64(q[k], w, w64, lin, cu[k]);
-      else recon2<T>(q[k], w, lin, cu[k]);
+      for (int k = 0; k < NC; ++k) {
+        Coef2<float> kc;
+        coef2<float, float>(q[k], kc);
+        if (lin) {
+#pragma unroll
+          for (int l = 0; l < 15; ++l) cu[k][l] = kc.c[l];
+          continue;
+        }
+        float a[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (redo == 0u) {
+          const bool quiet = screen2(q[k], kc, w64, w);
+          if (!__all_sync(HW_FULL_MASK, quiet)) {
+            pe |= 1u << k;
+            nb |= quiet ? 0u : 1u << k;
+          }
+        } else if ((redo >> k) & 1u) {
+#pragma unroll
+          for (int m = 0; m < 5; ++m) a[m] = a64[k][m];
+        }
+        float r, om[5];
+        finish2(a, w, r, om);
+        combine2<float>(kc, r, om, w, cu[k]);
+      }
+      if (pe != 0u) {
+        *pend = pe;
+        *nqb = nb;
+        return false;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) recon2<T>(q[k], w, lin, cu[k]);
     }
   }
   if constexpr (CHR) {
@@ -163,6 +308,7 @@ __device__ __forceinline__ void pass2d(const T* __restrict__ box, int bidx, int 
       vh[k] += sig[mu] * (UR[k] - UL[k]);
     }
   }
+  return true;
 }
 
 // Per-tile quantities: kernel-wide for one grid, the tile's instance in a
@@ -217,10 +363,11 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
     const T* src0 = in + (long long)(j0 - 2) * G.nx + (i0 - 2);
     for (int row = warp; row < NF * kBox; row += nwarps) {
       const int f = row / kBox, rr = row - f * kBox;
+      const int d = f / NC, k = f - d * NC;
       const T* srow = src0 + f * plane + (long long)rr * G.nx;
-      T* drow = box + f * kFS + rr * kBP;
-      cp_async_elem(drow + lane, srow + lane);
-      if (lane < kBox - 32) cp_async_elem(drow + 32 + lane, srow + 32 + lane);
+      T* drow = box + box_at<NC>(d, rr * kBP, k);
+      cp_async_elem(drow + lane * NC, srow + lane);
+      if (lane < kBox - 32) cp_async_elem(drow + (32 + lane) * NC, srow + 32 + lane);
     }
     cp_async_wait_all();
   } else {
@@ -231,7 +378,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       T v;
       if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
       else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j, c.t_bc);
-      box[f * kFS + rr * kBP + cc] = v;
+      box[box_at<NC>(f / NC, rr * kBP + cc, f % NC)] = v;
     }
   }
   __syncthreads();
@@ -242,8 +389,25 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   for (int D = 0; D < 2; ++D) {
     if (D == 1) __syncthreads();  // the x pass's stash is complete
     const int lines = D == 0 ? G.ny - j0 : G.nx - i0;
-    for (int r = warp; r < kT2; r += nwarps) {
-      if (r >= lines) break;
+    // the warp's rows r = warp + i nwarps; mixed precision: rows the screen
+    // does not clear are deferred (bit i of dmask; their fields and this
+    // lane's uncleared ones in byte i of dbits) and redone after the others
+    const int own = (min(kT2, lines) - warp + nwarps - 1) / nwarps;
+    unsigned dmask = 0u;
+    unsigned long long dbits = 0ull;
+    volatile float a64[W64 ? NC : 1][5];
+#pragma unroll 1
+    for (int t = 0;; ++t) {
+      int ri = t;
+      unsigned redo = 0u;
+      if (t >= own) {
+        if constexpr (!W64) break;
+        if (dmask == 0u) break;
+        ri = __ffs(dmask) - 1;
+        dmask &= dmask - 1u;
+        redo = (unsigned)(dbits >> (8 * ri)) & 0xffu;
+      }
+      const int r = warp + ri * nwarps;
       // learned indicator: a warp whose 32 cells are all smooth takes p0
       bool lin = lin_all;
       if (smooth != nullptr && !lin) {
@@ -261,9 +425,19 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         wp64.g[2] = D == 0 ? wx64.g[2] : wx64.g[4];
         wp64.g[4] = D == 0 ? wx64.g[4] : wx64.g[2];
       }
+      if constexpr (W64) {
+        if (redo != 0u)
+          pack64<NC, CHR>(box, bidx, D, CHR && !lin, g, redo & 0xfu, redo >> 4, wp64, a64);
+      }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
-                              D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh);
+      unsigned pend = 0u, nqb = 0u;
+      if (!pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
+                                   D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh,
+                                   redo & 0xfu, a64, &pend, &nqb)) {
+        dmask |= 1u << ri;
+        dbits |= (unsigned long long)(pend | (nqb << 4)) << (8 * ri);
+        continue;
+      }
       T Gu[NC], Gv[NC], Gw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
@@ -273,30 +447,38 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       }
       if (D == 0) {
         if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
-          const int sidx = stash_at<T>(r, lane - 1);
+          T su[NC], sv[NC], sw[NC];
 #pragma unroll
           for (int k = 0; k < NC; ++k) {
-            stash[(0 * NC + k) * kSS + sidx] = -(Gu[k] - Fu[k]) * idx;
-            stash[(1 * NC + k) * kSS + sidx] = -(Gv[k] - Fv[k]);
-            stash[(2 * NC + k) * kSS + sidx] = -(Gw[k] - Fw[k]) * dyx;
-            stash[(3 * NC + k) * kSS + sidx] = vh[k];
+            su[k] = -(Gu[k] - Fu[k]) * idx;
+            sv[k] = -(Gv[k] - Fv[k]);
+            sw[k] = -(Gw[k] - Fw[k]) * dyx;
           }
+          vec_store<T, NC>(stash + stash_at<T, NC>(0, r, lane - 1), su);
+          vec_store<T, NC>(stash + stash_at<T, NC>(1, r, lane - 1), sv);
+          vec_store<T, NC>(stash + stash_at<T, NC>(2, r, lane - 1), sw);
+          vec_store<T, NC>(stash + stash_at<T, NC>(3, r, lane - 1), vh);
         }
         continue;
       }
       const int cc = r, i = i0 + cc;
       const int j = j0 - 1 + lane;
       if (lane >= 1 && lane <= kT2 && j < G.ny) {
-        const int sidx = stash_at<T>(lane - 1, cc);
         const long long p = (long long)j * G.nx + i;
+        T xu[NC], xv[NC], xw[NC], xh[NC], ubox[NC];
+        vec_load<T, NC>(stash + stash_at<T, NC>(0, lane - 1, cc), xu);
+        vec_load<T, NC>(stash + stash_at<T, NC>(1, lane - 1, cc), xv);
+        vec_load<T, NC>(stash + stash_at<T, NC>(2, lane - 1, cc), xw);
+        vec_load<T, NC>(stash + stash_at<T, NC>(3, lane - 1, cc), xh);
+        if (a.stage != 0) vec_load<T, NC>(box + box_at<NC>(0, (lane + 1) * kBP + cc + 2, 0), ubox);
         T nu[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
           const int kk = frame_comp<1, EQ>(k);
-          const T Lu = stash[(0 * NC + k) * kSS + sidx] - (Gu[kk] - Fu[kk]) * idy;
-          const T Lv = stash[(1 * NC + k) * kSS + sidx] - (Gw[kk] - Fw[kk]) * dxy;
-          const T Lw = stash[(2 * NC + k) * kSS + sidx] - (Gv[kk] - Fv[kk]);
-          const T vx = stash[(3 * NC + k) * kSS + sidx];
+          const T Lu = xu[k] - (Gu[kk] - Fu[kk]) * idy;
+          const T Lv = xv[k] - (Gw[kk] - Fw[kk]) * dxy;
+          const T Lw = xw[k] - (Gv[kk] - Fv[kk]);
+          const T vx = xh[k];
           const T wyv = vh[kk];
           const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
           const long long hv = k * plane + p, hw_ = (NC + k) * plane + p;
@@ -304,8 +486,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
             out[iu] = Lu; out[iv] = Lv; out[iw] = Lw;
             hat[hv] = vx; hat[hw_] = wyv;
           } else {
-            const T ub = box[k * kFS + (lane + 1) * kBP + cc + 2];
-            const T su = ub + tdt * Lu, sv = vx + tdt * Lv, sw = wyv + tdt * Lw;
+            const T su = ubox[k] + tdt * Lu, sv = vx + tdt * Lv, sw = wyv + tdt * Lw;
             if (a.stage == 1) {
               out[iu] = su; out[iv] = sv; out[iw] = sw;
               hat[hv] = vx; hat[hw_] = wyv;
@@ -348,7 +529,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
 // run-time switches).  BATCH: the tiles of many 2D instances of uneven sizes
 // (a tile table; per-instance descriptors and control blocks).
 template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
-__global__ void __launch_bounds__(kThreads2, sizeof(T) == 4 ? 2 : 1) k_stage2d(const Stage2Args a) {
+__global__ void __launch_bounds__(threads2<T, W64>(), sizeof(T) == 4 ? 2 : 1) k_stage2d(const Stage2Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
   constexpr int NF = 3 * NC;
   extern __shared__ __align__(16) unsigned char hw_smem[];
@@ -496,7 +677,7 @@ struct Launch2 {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR, W64, FAST, BATCH>, kThreads2,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_stage2d<T, EQ, CHR, W64, FAST, BATCH>, threads2<T, W64>(),
                                                       smem);
     if (e != cudaSuccess) return e;
     if (n < 1) return cudaErrorInvalidConfiguration;
@@ -515,7 +696,7 @@ struct Launch2 {
     if (tiles < 1) return cudaSuccess;
     long long blocks = sh.persistent2d ? (long long)num_sms * per_sm : tiles;
     if (blocks > tiles) blocks = tiles;
-    k_stage2d<T, EQ, CHR, W64, FAST, BATCH><<<(unsigned)blocks, kThreads2, smem, st>>>(a);
+    k_stage2d<T, EQ, CHR, W64, FAST, BATCH><<<(unsigned)blocks, threads2<T, W64>(), smem, st>>>(a);
     return cudaGetLastError();
   }
 };
