@@ -68,9 +68,16 @@ __device__ __forceinline__ int stash_at(int q, int r, int c) {
 template <int NC>
 constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
 
+// Mixed precision: the rows of a pass that the FP32 screen did not clear,
+// listed by the warps that met them and shared out among all warps.
+struct DeferList {
+  int n[2];                  // per pass
+  unsigned char row[kT2 + 2];
+};
+
 template <typename T, int NC>
 constexpr size_t smem_bytes2() {
-  return sizeof(T) * (size_t)(3 * NC * kFS + stash_fields<NC>() * kSS);
+  return sizeof(T) * (size_t)(3 * NC * kFS + stash_fields<NC>() * kSS) + sizeof(DeferList);
 }
 
 // The halo box is cell-interleaved: group d (0 averages, 1 x-moments,

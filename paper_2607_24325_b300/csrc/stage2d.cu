@@ -337,7 +337,11 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   const long long plane = a.plane;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
+  DeferList* dl = reinterpret_cast<DeferList*>(stash + 4 * NC * kSS);  // after the stash
   __syncthreads();
+  if constexpr (W64) {
+    if (threadIdx.x == 0) dl->n[0] = dl->n[1] = 0;  // published by the fill's barrier
+  }
   const T* __restrict__ in = c.in;
   const T* base = c.base;
   T* out = c.out;
@@ -389,25 +393,40 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   for (int D = 0; D < 2; ++D) {
     if (D == 1) __syncthreads();  // the x pass's stash is complete
     const int lines = D == 0 ? G.ny - j0 : G.nx - i0;
-    // the warp's rows r = warp + i nwarps; mixed precision: rows the screen
-    // does not clear are deferred (bit i of dmask; their fields and this
-    // lane's uncleared ones in byte i of dbits) and redone after the others
+    // the warp's own rows r = warp + t nwarps first; mixed precision: a row
+    // the screen does not clear is listed (phase 0), and once every warp has
+    // listed its rows, the list is shared out: each listed row is screened
+    // again for its uncleared lanes (phase 1), its FP64 items packed and the
+    // row redone (phase 2)
     const int own = (min(kT2, lines) - warp + nwarps - 1) / nwarps;
-    unsigned dmask = 0u;
-    unsigned long long dbits = 0ull;
+    int t = 0, r = 0, e = warp, n_def = 0, phase = 0;
+    unsigned held = 0u;  // phase 2: the row's pending fields | this lane's uncleared ones << 4
     volatile float a64[W64 ? NC : 1][5];
 #pragma unroll 1
-    for (int t = 0;; ++t) {
-      int ri = t;
+    for (;;) {
       unsigned redo = 0u;
-      if (t >= own) {
-        if constexpr (!W64) break;
-        if (dmask == 0u) break;
-        ri = __ffs(dmask) - 1;
-        dmask &= dmask - 1u;
-        redo = (unsigned)(dbits >> (8 * ri)) & 0xffu;
+      if (phase == 0) {
+        if (t < own) {
+          r = warp + t * nwarps;
+          ++t;
+        } else {
+          if constexpr (!W64) {
+            break;
+          } else {
+            __syncthreads();  // every warp's deferred rows are listed
+            n_def = dl->n[D];
+            phase = 1;
+            continue;
+          }
+        }
+      } else if (phase == 1) {
+        if (e >= n_def) break;
+        r = dl->row[e];
+        e += nwarps;
+      } else {
+        redo = held;
+        phase = 1;
       }
-      const int r = warp + ri * nwarps;
       // learned indicator: a warp whose 32 cells are all smooth takes p0
       bool lin = lin_all;
       if (smooth != nullptr && !lin) {
@@ -434,8 +453,12 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       if (!pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
                                    D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh,
                                    redo & 0xfu, a64, &pend, &nqb)) {
-        dmask |= 1u << ri;
-        dbits |= (unsigned long long)(pend | (nqb << 4)) << (8 * ri);
+        if (phase == 0) {
+          if (lane == 0) dl->row[atomicAdd(&dl->n[D], 1)] = (unsigned char)r;
+        } else {
+          held = pend | (nqb << 4);
+          phase = 2;
+        }
         continue;
       }
       T Gu[NC], Gv[NC], Gw[NC];
