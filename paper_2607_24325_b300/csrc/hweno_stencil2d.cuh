@@ -469,7 +469,9 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
 
 // Steps 2-3, the weights from a_m (0 where screened, else indicator64):
 // w~_m = gamma_m (1 + a_m) and the normalisation in FP32 (every term
-// positive: a few FP32 ulp at most), r = omega_0 / gamma_0 and om[1..4].
+// positive: a few FP32 ulp at most), r = omega_0 / gamma_0 and om[1..4],
+// materialised, so that weights from a_m = 0 read the same wherever they
+// were formed.
 __device__ __forceinline__ void finish2(const float* a, const WeightsT<float>& wf, float& r, float* om) {
   float e[5], sum = 0.0f;
 #pragma unroll
@@ -478,9 +480,9 @@ __device__ __forceinline__ void finish2(const float* a, const WeightsT<float>& w
     sum += e[m];
   }
   const float inv = rcp_approx(sum);
-  r = (1.0f + a[0]) * inv;
+  r = opaque((1.0f + a[0]) * inv);
 #pragma unroll
-  for (int m = 1; m <= 4; ++m) om[m] = e[m] * inv;
+  for (int m = 1; m <= 4; ++m) om[m] = opaque(e[m] * inv);
 }
 
 // Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)

@@ -212,6 +212,12 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
       // FP32 coefficients and weights; a_m = 0 where the screen clears the
       // whole warp, from a64 in a redone row
       unsigned pe = 0u, nb = 0u;
+      // the weights of a cleared field (every a_m = 0), once per row
+      float r0, om0[5];
+      {
+        const float z[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        finish2(z, w, r0, om0);
+      }
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         Coef2<float> kc;
@@ -221,7 +227,9 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
           for (int l = 0; l < 15; ++l) cu[k][l] = kc.c[l];
           continue;
         }
-        float a[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        float r = r0, om[5];
+#pragma unroll
+        for (int m = 1; m < 5; ++m) om[m] = om0[m];
         if (redo == 0u) {
           const bool quiet = screen2(q[k], kc, w64, w);
           if (!__all_sync(HW_FULL_MASK, quiet)) {
@@ -229,11 +237,11 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
             nb |= quiet ? 0u : 1u << k;
           }
         } else if ((redo >> k) & 1u) {
+          float a[5];
 #pragma unroll
           for (int m = 0; m < 5; ++m) a[m] = a64[k][m];
+          finish2(a, w, r, om);
         }
-        float r, om[5];
-        finish2(a, w, r, om);
         combine2<float>(kc, r, om, w, cu[k]);
       }
       if (pe != 0u) {
