@@ -180,6 +180,25 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest x over all ranks (a job's time is its slowest rank's);
+    x itself when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds: float, world: int) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' units over the
+    slowest rank's time (every rank calls it: it reduces across ranks)."""
+    return world * units_per_rank / max_over_ranks(seconds)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -568,12 +587,10 @@ def main():
         arms[name]["variant"] = extra
     head_name = "fp32_ind64" if "fp32_ind64" in arms else next(iter(arms))
     head = arms[head_name]
+    for name in arms:   # every rank, same order: each arm's time is its slowest rank's
+        arms[name]["ms"] = max_over_ranks(arms[name]["ms"])
     ms_head = head["ms"]
-    if world > 1:
-        x = torch.tensor([ms_head], device="cuda", dtype=torch.float64)
-        dist.all_reduce(x, op=dist.ReduceOp.MAX)
-        ms_head = float(x.item())
-    value = world * ncells * 3 * args.steps / (ms_head * 1e-3)
+    value = job_rate(ncells * 3 * args.steps, ms_head * 1e-3, world)
     ref_rho = arms["fp64"]["rho"] if "fp64" in arms else None
 
     # end to end with host buffers
@@ -582,7 +599,7 @@ def main():
         prec = head["precision"]
         src = U0_pin if prec == hw.FP64 else U0_t.float().pin_memory()
         e2e_s, nbytes, _ = e2e_run(hw, torch, src, prec, args.steps)
-        e2e = {"value": world * ncells * 3 * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": job_rate(ncells * 3 * args.steps, e2e_s, world), "unit": UNIT,
                "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                "what": "set_state from pinned host + advance + get_state to pinned host, per step"}
 
