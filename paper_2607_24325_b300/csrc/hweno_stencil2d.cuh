@@ -69,10 +69,16 @@ template <int NC>
 constexpr int stash_fields() { return 4 * NC; }   // L_u, L_v, L_w, v-hat
 
 // Mixed precision: the rows of a pass that the FP32 screen did not clear,
-// listed by the warps that met them and shared out among all warps.
+// listed by the warps that met them and shared out among all warps.  The
+// first kDeferBal entries also keep, per field, the ballot of the lanes the
+// screen did not clear (0 for a cleared field), so the warp that redoes the
+// row needs no second screen; later entries are screened again (shared
+// memory is nearly full at two CTAs per SM).
+constexpr int kDeferBal = 24;
 struct DeferList {
   int n[2];                  // per pass
   unsigned char row[kT2 + 2];
+  unsigned bal[kDeferBal][4];
 };
 
 template <typename T, int NC>

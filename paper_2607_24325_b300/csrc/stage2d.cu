@@ -430,6 +430,16 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       } else if (phase == 1) {
         if (e >= n_def) break;
         r = dl->row[e];
+        if (e < kDeferBal) {  // the listing warp's ballots: straight to the redo
+          unsigned pd = 0u, nb = 0u;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const unsigned b = dl->bal[e][k];
+            pd |= (b != 0u ? 1u : 0u) << k;
+            nb |= ((b >> lane) & 1u) << k;
+          }
+          redo = pd | (nb << 4);
+        }
         e += nwarps;
       } else {
         redo = held;
@@ -462,7 +472,19 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
                                    D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh,
                                    redo & 0xfu, a64, &pend, &nqb)) {
         if (phase == 0) {
-          if (lane == 0) dl->row[atomicAdd(&dl->n[D], 1)] = (unsigned char)r;
+          int slot = 0;
+          if (lane == 0) {
+            slot = atomicAdd(&dl->n[D], 1);
+            dl->row[slot] = (unsigned char)r;
+          }
+          slot = __shfl_sync(HW_FULL_MASK, slot, 0);
+          if (slot < kDeferBal) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+              const unsigned b = __ballot_sync(HW_FULL_MASK, (nqb >> k) & 1u);
+              if (lane == 0) dl->bal[slot][k] = b;
+            }
+          }
         } else {
           held = pend | (nqb << 4);
           phase = 2;
