@@ -272,7 +272,7 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
 // ---------------------------------------------------------------------------
 template <typename T>
 struct Eig {
-  T u, v, c, H, q2h, b1, ic;  // q2h = (u^2+v^2)/2, b1 = (g-1)/c^2, ic = 1/c
+  T u, v, c, H, q2h, hb1, hic;  // q2h = (u^2+v^2)/2, hb1 = (g-1)/(2c^2), hic = 1/(2c)
 };
 
 template <typename T>
@@ -285,9 +285,10 @@ __device__ __forceinline__ Eig<T> eig1(T r, T m, T E, T g) {
   const T p = (g - T(1)) * (E - m * e.u * T(0.5));
   const T c2 = g * p * ir;
   e.c = sqrt_t(c2);
-  e.ic = rcp_t(e.c);
+  const T ic = rcp_t(e.c);
+  e.hic = T(0.5) * ic;
   e.H = (E + p) * ir;
-  e.b1 = (g - T(1)) * e.ic * e.ic;
+  e.hb1 = (T(0.5) * (g - T(1))) * ic * ic;
   return e;
 }
 
@@ -301,20 +302,23 @@ __device__ __forceinline__ Eig<T> eig2(T r, T mx, T my, T E, T g) {
   const T p = (g - T(1)) * (E - r * e.q2h);
   const T c2 = g * p * ir;
   e.c = sqrt_t(c2);
-  e.ic = rcp_t(e.c);
+  const T ic = rcp_t(e.c);
+  e.hic = T(0.5) * ic;
   e.H = (E + p) * ir;
-  e.b1 = (g - T(1)) * e.ic * e.ic;
+  e.hb1 = (T(0.5) * (g - T(1))) * ic * ic;
   return e;
 }
 
 // 1D: left eigenvectors applied to x (characteristic variables w = L x).
 template <typename T>
 __device__ __forceinline__ void l1_apply(const Eig<T>& e, const T* x, T* w) {
-  const T s = e.b1 * (e.q2h * x[0] - e.u * x[1] + x[2]);
-  const T t = (e.u * x[0] - x[1]) * e.ic;
-  w[0] = T(0.5) * (s + t);
-  w[1] = x[0] - s;
-  w[2] = T(0.5) * (s - t);
+  // sh, th: half the usual s, t (the halves of L's first and last rows
+  // folded into the per-cell scales; exact, powers of two)
+  const T sh = e.hb1 * (e.q2h * x[0] - e.u * x[1] + x[2]);
+  const T th = (e.u * x[0] - x[1]) * e.hic;
+  w[0] = sh + th;
+  w[1] = x[0] - T(2) * sh;
+  w[2] = sh - th;
 }
 // 1D: right eigenvectors, y = R w.
 template <typename T>
@@ -329,13 +333,13 @@ __device__ __forceinline__ void r1_apply(const Eig<T>& e, const T* w, T* y) {
 // 2D, direction D (0: x, 1: y): w = L_D x.
 template <int D, typename T>
 __device__ __forceinline__ void l2_apply(const Eig<T>& e, const T* x, T* w) {
-  const T s = e.b1 * (e.q2h * x[0] - e.u * x[1] - e.v * x[2] + x[3]);
+  const T sh = e.hb1 * (e.q2h * x[0] - e.u * x[1] - e.v * x[2] + x[3]);  // half of s
   const T un = D == 0 ? e.u : e.v;
-  const T t = (un * x[0] - x[1 + D]) * e.ic;
-  w[0] = T(0.5) * (s + t);
-  w[1] = x[0] - s;
+  const T th = (un * x[0] - x[1 + D]) * e.hic;                              // half of t
+  w[0] = sh + th;
+  w[1] = x[0] - T(2) * sh;
   w[2] = D == 0 ? x[2] - e.v * x[0] : x[1] - e.u * x[0];
-  w[3] = T(0.5) * (s - t);
+  w[3] = sh - th;
 }
 // 2D, direction D: y = R_D w.
 template <int D, typename T>

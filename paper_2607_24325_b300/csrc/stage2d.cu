@@ -26,8 +26,8 @@ namespace hw {
 
 static_assert(kT2 == kTile2, "host tile table and kernel tile size differ");
 
-// Lax-Friedrichs fluxes of the pass-frame x physics at one point:
-// f, f'(u) v (normal moment), f'(u) w (tangential moment).
+// Lax-Friedrichs fluxes of the pass-frame x physics at one point, doubled:
+// 2 f, 2 f'(u) v (normal moment), 2 f'(u) w (tangential moment).
 template <typename T, int NC, int EQ>
 __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, const T* Up, const T* Vp,
                                          const T* Wp, T alpha, T g, T adv, T* fu, T* fv, T* fw) {
@@ -42,12 +42,12 @@ __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, 
     Fm[0] = adv * Um[0]; HVm[0] = adv * Vm[0]; HWm[0] = adv * Wm[0];
     Fp[0] = adv * Up[0]; HVp[0] = adv * Vp[0]; HWp[0] = adv * Wp[0];
   }
-  const T ha = T(0.5) * alpha;
+  // twice the flux: the 1/2 is folded into the Gauss weights by the caller
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    fu[k] = T(0.5) * (Fm[k] + Fp[k]) - ha * (Up[k] - Um[k]);
-    fv[k] = T(0.5) * (HVm[k] + HVp[k]) - ha * (Vp[k] - Vm[k]);
-    fw[k] = T(0.5) * (HWm[k] + HWp[k]) - ha * (Wp[k] - Wm[k]);
+    fu[k] = (Fm[k] + Fp[k]) - alpha * (Up[k] - Um[k]);
+    fv[k] = (HVm[k] + HVp[k]) - alpha * (Vp[k] - Vm[k]);
+    fw[k] = (HWm[k] + HWp[k]) - alpha * (Wp[k] - Wm[k]);
   }
 }
 
@@ -273,6 +273,7 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
 #pragma unroll
   for (int k = 0; k < NC; ++k) { Fu[k] = T(0); Fv[k] = T(0); Fw[k] = T(0); vh[k] = T(0); }
   const T sig[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+  const T hsig[3] = {T(5.0 / 36.0), T(8.0 / 36.0), T(5.0 / 36.0)};  // with lf_point's 1/2
   FacePts<T> fr[NC], fl[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
@@ -310,9 +311,9 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
     lf_point<T, NC, EQ>(Um, Vm, Wm, UL, VL, WL, alpha, g, adv, fu, fv, fw);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      Fu[k] += sig[mu] * fu[k];
-      Fv[k] += sig[mu] * fv[k];
-      Fw[k] += sig[mu] * fw[k];
+      Fu[k] += hsig[mu] * fu[k];
+      Fv[k] += hsig[mu] * fv[k];
+      Fw[k] += hsig[mu] * fw[k];
       vh[k] += sig[mu] * (UR[k] - UL[k]);
     }
   }
