@@ -294,10 +294,10 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
       T* Uo = side == 0 ? UR : UL;
       T* Vo = side == 0 ? VR : VL;
       T* Wo = side == 0 ? WR : WL;
+      // derivatives per unit xi, eta: the moment fluxes are linear in them,
+      // so the 1/h scales are applied once to the Gauss sums below
 #pragma unroll
       for (int k = 0; k < NC; ++k) { Uo[k] = u[k]; Vo[k] = un[k]; Wo[k] = ut[k]; }
-#pragma unroll
-      for (int k = 0; k < NC; ++k) { Vo[k] *= ihn; Wo[k] *= iht; }
     }
     // left neighbour's right-face state at this Gauss point
     T Um[NC], Vm[NC], Wm[NC];
@@ -316,6 +316,11 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
       Fw[k] += hsig[mu] * fw[k];
       vh[k] += sig[mu] * (UR[k] - UL[k]);
     }
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    Fv[k] *= ihn;
+    Fw[k] *= iht;
   }
   return true;
 }
