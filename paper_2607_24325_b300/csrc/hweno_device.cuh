@@ -15,6 +15,42 @@
 namespace hw {
 
 // ---------------------------------------------------------------------------
+// Checked build (compiled with -DHWENO_CHECKED into libhweno_checked.so): the
+// shared- and global-memory indices of the stage kernels are tested against
+// their buffers' extents; a bad one is counted, the first is recorded (site,
+// index, extent) in this translation unit's check word, and the access is
+// skipped (a load gives 0).  No trap, no assert: the context stays usable and
+// the host reads the word (hweno_check_*).  In the normal build HW_IN is
+// `true` and costs nothing.
+// ---------------------------------------------------------------------------
+#ifdef HWENO_CHECKED
+static __device__ unsigned int hw_check[4];  // bad accesses, first site, its index, its extent
+__device__ __forceinline__ bool hw_in(long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (atomicAdd(&hw_check[0], 1u) == 0u) {
+    hw_check[1] = (unsigned)site;
+    hw_check[2] = (unsigned)i;
+    hw_check[3] = (unsigned)n;
+  }
+  return false;
+}
+#define HW_IN(i, n, site) ::hw::hw_in((long long)(i), (long long)(n), (site))
+// host side: copy (and optionally clear) this translation unit's check word
+#define HW_CHECK_READER(name)                                                        \
+  extern "C" int name(unsigned int* out4, int reset) {                               \
+    cudaError_t e = cudaMemcpyFromSymbol(out4, ::hw::hw_check, sizeof(unsigned) * 4); \
+    if (e == cudaSuccess && reset) {                                                 \
+      const unsigned z[4] = {0u, 0u, 0u, 0u};                                        \
+      e = cudaMemcpyToSymbol(::hw::hw_check, z, sizeof z);                           \
+    }                                                                                \
+    return (int)e;                                                                   \
+  }
+#else
+#define HW_IN(i, n, site) true
+#define HW_CHECK_READER(name)
+#endif
+
+// ---------------------------------------------------------------------------
 // Scheme parameters in the arithmetic type T.
 // ---------------------------------------------------------------------------
 template <typename T>

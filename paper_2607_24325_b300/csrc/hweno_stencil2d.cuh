@@ -99,11 +99,34 @@ __device__ __forceinline__ int box_at(int d, int cell, int k) {
 // pass swaps the momentum components).
 template <typename T, int NC>
 __device__ __forceinline__ void box_load(const T* __restrict__ box, int d, int cell, int D, T* x) {
-  vec_load<T, NC>(box + box_at<NC>(d, cell, 0), x);
+  const int at = box_at<NC>(d, cell, 0);
+  if (!HW_IN(at, 3 * NC * kFS - NC + 1, 1)) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x[k] = T(0);
+    return;
+  }
+  vec_load<T, NC>(box + at, x);
   if constexpr (NC == 4) {
     const T a = x[1], b = x[2];
     x[1] = D == 0 ? a : b;
     x[2] = D == 0 ? b : a;
+  }
+}
+
+// The NC components of tile cell (r, c) of stash quantity q.
+template <typename T, int NC>
+__device__ __forceinline__ void stash_store(T* stash, int q, int r, int c, const T* x) {
+  const int at = stash_at<T, NC>(q, r, c);
+  if (HW_IN(at, 4 * NC * kSS - NC + 1, 2)) vec_store<T, NC>(stash + at, x);
+}
+template <typename T, int NC>
+__device__ __forceinline__ void stash_load(const T* stash, int q, int r, int c, T* x) {
+  const int at = stash_at<T, NC>(q, r, c);
+  if (HW_IN(at, 4 * NC * kSS - NC + 1, 3)) {
+    vec_load<T, NC>(stash + at, x);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) x[k] = T(0);
   }
 }
 

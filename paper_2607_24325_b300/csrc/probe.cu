@@ -76,3 +76,28 @@ extern "C" hweno_status hweno_peak_fma(int precision, double* flops_per_second) 
   *flops_per_second = f;
   return f > 0.0 ? HWENO_OK : HWENO_ERR_CUDA;
 }
+
+#ifdef HWENO_CHECKED
+// The checked build's index test itself: one index inside its extent (not
+// recorded) and one outside (recorded as site 99, index 7, extent 5).  No
+// memory is accessed at either index.
+namespace {
+__global__ void k_check_selftest(int* out) {
+  out[0] = HW_IN(3, 5, 98) ? 1 : 0;
+  out[1] = HW_IN(7, 5, 99) ? 1 : 0;
+}
+}  // namespace
+
+HW_CHECK_READER(hweno_check_probe)
+
+extern "C" int hweno_check_selftest(int* pass_out) {
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+  if (e != cudaSuccess) return (int)e;
+  k_check_selftest<<<1, 1>>>(d);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpy(pass_out, d, 2 * sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return (int)e;
+}
+#endif

@@ -32,6 +32,11 @@ __device__ __forceinline__ void load_cell1(const T* __restrict__ in, long long t
     return;
   }
   const long long p = I.off + g.src;
+  if (!(HW_IN(g.src, I.n, 21) && HW_IN(p, total, 21))) {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) ub[k] = vb[k] = T(0);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     T u = in[k * total + p];
@@ -158,7 +163,8 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
       Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
       Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
     }
-    const bool interior = lane >= 1 && lane <= kTile1 && cell < I.n;
+    const bool interior = lane >= 1 && lane <= kTile1 && cell < I.n && HW_IN(cell, I.n, 22) &&
+                          HW_IN(I.off + cell, total, 22);
     double rad = 0.0;
     if (interior) {
       const long long p = I.off + cell;
@@ -280,3 +286,5 @@ cudaError_t launch_alpha1d(int precision, int equation, const void* U, long long
 }
 
 }  // namespace hw
+
+HW_CHECK_READER(hweno_check_stage1d)

@@ -383,9 +383,14 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       const int f = row / kBox, rr = row - f * kBox;
       const int d = f / NC, k = f - d * NC;
       const T* srow = src0 + f * plane + (long long)rr * G.nx;
-      T* drow = box + box_at<NC>(d, rr * kBP, k);
-      cp_async_elem(drow + lane * NC, srow + lane);
-      if (lane < kBox - 32) cp_async_elem(drow + (32 + lane) * NC, srow + 32 + lane);
+      const int at = box_at<NC>(d, rr * kBP, k);
+      T* drow = box + at;
+      const bool row_ok = HW_IN(j0 - 2 + rr, G.ny, 6);
+      if (row_ok && HW_IN(at + lane * NC, 3 * NC * kFS, 5) && HW_IN(i0 - 2 + lane, G.nx, 6))
+        cp_async_elem(drow + lane * NC, srow + lane);
+      if (lane < kBox - 32 && row_ok && HW_IN(at + (32 + lane) * NC, 3 * NC * kFS, 5) &&
+          HW_IN(i0 + 30 + lane, G.nx, 6))
+        cp_async_elem(drow + (32 + lane) * NC, srow + 32 + lane);
     }
     cp_async_wait_all();
   } else {
@@ -396,7 +401,8 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       T v;
       if (i >= 0 && i < G.nx && j >= 0 && j < G.ny) v = in[f * plane + (long long)j * G.nx + i];
       else v = load_ghost2<T, EQ, NC>(in, plane, G, f, i, j, c.t_bc);
-      box[box_at<NC>(f / NC, rr * kBP + cc, f % NC)] = v;
+      const int at = box_at<NC>(f / NC, rr * kBP + cc, f % NC);
+      if (HW_IN(at, 3 * NC * kFS, 7)) box[at] = v;
     }
   }
   __syncthreads();
@@ -435,7 +441,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         }
       } else if (phase == 1) {
         if (e >= n_def) break;
-        r = dl->row[e];
+        r = HW_IN(e, kT2 + 2, 11) ? dl->row[e] : 0;
         if (e < kDeferBal) {  // the listing warp's ballots: straight to the redo
           unsigned pd = 0u, nb = 0u;
 #pragma unroll
@@ -481,7 +487,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
           int slot = 0;
           if (lane == 0) {
             slot = atomicAdd(&dl->n[D], 1);
-            dl->row[slot] = (unsigned char)r;
+            if (HW_IN(slot, kT2 + 2, 10)) dl->row[slot] = (unsigned char)r;
           }
           slot = __shfl_sync(HW_FULL_MASK, slot, 0);
           if (slot < kDeferBal) {
@@ -513,23 +519,23 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
             sv[k] = -(Gv[k] - Fv[k]);
             sw[k] = -(Gw[k] - Fw[k]) * dyx;
           }
-          vec_store<T, NC>(stash + stash_at<T, NC>(0, r, lane - 1), su);
-          vec_store<T, NC>(stash + stash_at<T, NC>(1, r, lane - 1), sv);
-          vec_store<T, NC>(stash + stash_at<T, NC>(2, r, lane - 1), sw);
-          vec_store<T, NC>(stash + stash_at<T, NC>(3, r, lane - 1), vh);
+          stash_store<T, NC>(stash, 0, r, lane - 1, su);
+          stash_store<T, NC>(stash, 1, r, lane - 1, sv);
+          stash_store<T, NC>(stash, 2, r, lane - 1, sw);
+          stash_store<T, NC>(stash, 3, r, lane - 1, vh);
         }
         continue;
       }
       const int cc = r, i = i0 + cc;
       const int j = j0 - 1 + lane;
-      if (lane >= 1 && lane <= kT2 && j < G.ny) {
+      if (lane >= 1 && lane <= kT2 && j < G.ny && HW_IN(i, G.nx, 9) && HW_IN(j, G.ny, 9)) {
         const long long p = (long long)j * G.nx + i;
         T xu[NC], xv[NC], xw[NC], xh[NC], ubox[NC];
-        vec_load<T, NC>(stash + stash_at<T, NC>(0, lane - 1, cc), xu);
-        vec_load<T, NC>(stash + stash_at<T, NC>(1, lane - 1, cc), xv);
-        vec_load<T, NC>(stash + stash_at<T, NC>(2, lane - 1, cc), xw);
-        vec_load<T, NC>(stash + stash_at<T, NC>(3, lane - 1, cc), xh);
-        if (a.stage != 0) vec_load<T, NC>(box + box_at<NC>(0, (lane + 1) * kBP + cc + 2, 0), ubox);
+        stash_load<T, NC>(stash, 0, lane - 1, cc, xu);
+        stash_load<T, NC>(stash, 1, lane - 1, cc, xv);
+        stash_load<T, NC>(stash, 2, lane - 1, cc, xw);
+        stash_load<T, NC>(stash, 3, lane - 1, cc, xh);
+        if (a.stage != 0) box_load<T, NC>(box, 0, (lane + 1) * kBP + cc + 2, 0, ubox);
         T nu[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -844,3 +850,5 @@ cudaError_t launch_alpha2d(int precision, int equation, const void* U, long long
 }
 
 }  // namespace hw
+
+HW_CHECK_READER(hweno_check_stage2d)

@@ -18,10 +18,10 @@ def built():
     __graft_entry__.build()
 
 
-def _declared():
+def _declared(checked_only=False):
     names = []
     for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if fn.endswith(".h"):
+        if fn.endswith(".h") and (fn == "hweno_checked.h") == checked_only:
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
             names += re.findall(r"\b(hweno_\w+)\s*\(", txt)
@@ -40,6 +40,21 @@ def test_every_declared_symbol_is_exported():
     for n in declared:
         assert getattr(lib, n) is not None
     assert set(hw.EXPORTS) == set(declared)
+
+
+def test_checked_build_exports_both_headers():
+    """libhweno_checked.so: every entry point of the normal library plus the
+    check-word readers of include/hweno_checked.h."""
+    from paper_2607_24325_b300 import build as B
+    declared = _declared() + _declared(checked_only=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB_CHECKED], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\sT\s(hweno_\w+)", out))
+    missing = [n for n in declared if n not in exported]
+    assert not missing, missing
+    plain = subprocess.run(["nm", "-D", "--defined-only", hw.LIB_PATH], capture_output=True, text=True,
+                           check=True).stdout
+    assert not [n for n in _declared(checked_only=True) if re.search(rf"\sT\s{n}\b", plain)]
 
 
 def test_version_and_error_string():

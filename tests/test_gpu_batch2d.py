@@ -148,3 +148,30 @@ def test_batch2d_autotune_and_time_dependent_boundary():
     assert n[0] == nr and abs(t[0] - tr) < 1e-15
     for f in range(4):
         assert np.abs(got[0][f] - ref[f]).mean() < 1e-10 * np.abs(ref[f]).mean(), f
+
+
+def test_mixed_run_single_solver_matches_one_instance_batch():
+    """Many mixed-precision steps of a four-quadrant problem whose tiles next
+    to the discontinuities defer rows to the FP64 indicator: the single-grid
+    kernel (compile-time form of the paper's configuration) and the batch
+    kernel (run-time switches, tile table) take the same steps and agree to
+    FP32 rounding (a lost, doubled or misplaced tile or row would not)."""
+    nx, ny = 150, 120
+    p = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny, lin_w=W2D, bc=(1, 1, 1, 1))
+    U0 = W.quadrant_2d(W.quadrant_states(31), 0.37, 0.61, 0, 1, 0, 1, nx, ny)
+    cfg = cfg_from(p, hw.FP32_IND64)
+    s = hw.Solver(cfg)
+    s.set_state(U0)
+    t1, n1 = s.advance(0.05)
+    one = s.get_state(device=False)
+    s.close()
+    b = hw.Batch([cfg])
+    b.set_state(torch.from_numpy(b.pack([U0.astype(np.float32).astype(np.float64)])).cuda())
+    t2, n2 = b.advance([0.05])
+    two = b.unpack(b.get_state())[0]
+    b.close()
+    assert n1 == n2[0] and n1 >= 12
+    for f in range(4):
+        scale = np.abs(one[f]).max()
+        assert np.abs(one[f] - two[f]).max() <= 1e-3 * scale, f
+        assert np.abs(one[f] - two[f]).mean() <= 1e-5 * scale, f
