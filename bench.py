@@ -57,7 +57,7 @@ FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launch
                 "for the fp64 arm, FP32 flops of the fp32 kernel for the fp32 and fp32_ind64 arms")
 # DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
 # the bench grid by cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 656.2e6 / 1536 ** 2, "fp32": 336.9e6 / 1536 ** 2, "fp32_ind64": 344.1e6 / 1536 ** 2}
+TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 337.2e6 / 1536 ** 2, "fp32_ind64": 343.7e6 / 1536 ** 2}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 1536^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)

@@ -16,9 +16,12 @@ constexpr int kFS = kBox * kBP;   // box group stride, in cells
 constexpr int kSP = 30;           // stash pitch, in cells
 constexpr int kSS = kT2 * kSP + 8;  // stash quantity stride, in cells (room for the row skew)
 // Threads per stage-kernel CTA (two CTAs per SM in FP32, one in FP64).
-// The tile's 30 rows per pass are dealt to the warps in turn.
+// The tile's 30 rows per pass are dealt to the warps in turn.  Measured on
+// the mixed and FP32 kernels: 8 warps at 128 registers beat 6 or 5 warps
+// at 168 registers and 10 warps at 96 (fewer warps hide less latency; 96
+// registers spill).
 template <typename T, bool W64>
-constexpr int threads2() { return W64 ? 256 : 256; }
+constexpr int threads2() { return 256; }
 
 // The NC components of one cell as vector loads / stores (16-byte accesses
 // for the four Euler components; the address must be 16-byte aligned).
@@ -441,7 +444,7 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
   // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  For the
   // moment form (weights w_l summing to 1331) Cauchy-Schwarz gives
   // G = 2 sum_l w_l |c~_l| <= 2 sqrt(1331 A) <= 72.97 sqrt(beta~_0), taken
-  // as 73 sqrt(beta~_0).  Where the bound puts every a_m below 2^-28 for
+  // as 73 sqrt(beta~_0); likewise for the Jiang-Shu form with its matrix.  Where the bound puts every a_m below 2^-28 for
   // all 32 lanes, 1 + a_m is 1 in FP32 whatever the FP64 evaluation gives,
   // so that evaluation is skipped and the result is the same bit for bit
   // (any sound bound keeps this; a looser one only skips less often).
@@ -462,9 +465,9 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
       for (int l = 0; l < 15; ++l) ac[l] = fabsf(c[l]);
       bs[0] = beta_typical_2d(c);
       const float A = beta_typical_2d(ac);
-      const float G = 2.667f * (ac[1] + ac[2]) + 13.59f * (ac[3] + ac[5]) + 3.467f * ac[4] +
-                      78.77f * (ac[6] + ac[9]) + 9.623f * (ac[7] + ac[8]) + 1256.3f * (ac[10] + ac[14]) +
-                      85.46f * (ac[11] + ac[13]) + 39.92f * ac[12];
+      // G = 2 sum_l R_l |c~_l| <= 2 sqrt(R^T M^-1 R) sqrt(A), M the form's
+      // (positive definite) matrix: 2 sqrt(R^T M^-1 R) = 76.63, taken as 76.7
+      const float G = 76.7f * sqrt_approx(A);
       Ds[0] = 0x1p-18f * A + E * (G + 1469.0f * E);
     } else {
       bs[0] = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
