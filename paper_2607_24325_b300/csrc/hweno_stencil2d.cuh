@@ -54,10 +54,10 @@ __device__ __forceinline__ void vec_store(T* p, const T* x) {
   }
 }
 
-// The stash holds the x pass's results per tile cell: quantity q (L_u,
-// L_v, L_w, v-hat), then the cell, then its NC components.  The x pass
-// writes rows (consecutive lanes, consecutive cells); the y pass reads
-// columns (lane = row, stride kSP cells).  A stride of 30 cells alone puts
+// The stash holds the y pass's results per tile cell: quantity q (L_u,
+// L_v, L_w, w-hat), then the cell, then its NC components.  The y pass
+// writes columns (lane = row, stride kSP cells); the x pass reads rows
+// (consecutive lanes, consecutive cells).  A stride of 30 cells alone puts
 // lanes 4 rows apart (16-byte cells: 8 to a 128-byte line) or 16 rows apart
 // (4-byte cells) on one bank; skewing the rows by one cell every 4 (16 and
 // 32-byte cells), 8 (8-byte) or 16 (4-byte) rows spreads a column walk

@@ -364,7 +364,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   const T idx = c.idx, idy = c.idy, dyx = c.dyx, dxy = c.dxy, tdt = c.tdt;
   const bool inner = i0 >= 2 && j0 >= 2 && i0 + kBox - 2 <= G.nx && j0 + kBox - 2 <= G.ny;
   if (a.stage >= 2) {
-    // The y pass's stage update reads base and hat at the tile's cells:
+    // The x pass's stage update reads base and hat at the tile's cells:
     // start pulling those rows into L2 now (3 points cover every 128-byte
     // line of a 30-cell row in either precision).
     for (int e = threadIdx.x; e < 3 * NC * kT2 * 3; e += blockDim.x) {
@@ -407,11 +407,15 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   }
   __syncthreads();
 
-  // ---- x pass (D = 0): one row per warp iteration, lane l <-> cell i0-1+l;
-  // ---- y pass (D = 1) on the transposed box: one column per iteration.
+  // ---- y pass first (D = 1, on the transposed box: one column per warp
+  // iteration, lane l <-> cell j0-1+l), its share of L to the stash; then the
+  // x pass (D = 0: one row per iteration, lane l <-> cell i0-1+l) and the
+  // stage update, whose global loads and stores then run along x
+  // (consecutive lanes, consecutive addresses: whole 128-byte lines).
 #pragma unroll 1
-  for (int D = 0; D < 2; ++D) {
-    if (D == 1) __syncthreads();  // the x pass's stash is complete
+  for (int it = 0; it < 2; ++it) {
+    const int D = 1 - it;
+    if (it == 1) __syncthreads();  // the y pass's stash is complete
     const int lines = D == 0 ? G.ny - j0 : G.nx - i0;
     // the warp's own rows r = warp + t nwarps first; mixed precision: a row
     // the screen does not clear is listed (phase 0), and once every warp has
@@ -510,41 +514,42 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
         Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
       }
-      if (D == 0) {
-        if (lane >= 1 && lane <= kT2 && i0 - 1 + lane < G.nx) {
-          T su[NC], sv[NC], sw[NC];
+      if (it == 0) {  // y pass: column r, lane l <-> tile row l - 1; physical components
+        if (lane >= 1 && lane <= kT2 && j0 - 1 + lane < G.ny) {
+          T su[NC], sv[NC], sw[NC], sh[NC];
 #pragma unroll
           for (int k = 0; k < NC; ++k) {
-            su[k] = -(Gu[k] - Fu[k]) * idx;
-            sv[k] = -(Gv[k] - Fv[k]);
-            sw[k] = -(Gw[k] - Fw[k]) * dyx;
+            const int kk = frame_comp<1, EQ>(k);
+            su[k] = -(Gu[kk] - Fu[kk]) * idy;
+            sv[k] = -(Gw[kk] - Fw[kk]) * dxy;
+            sw[k] = -(Gv[kk] - Fv[kk]);
+            sh[k] = vh[kk];
           }
-          stash_store<T, NC>(stash, 0, r, lane - 1, su);
-          stash_store<T, NC>(stash, 1, r, lane - 1, sv);
-          stash_store<T, NC>(stash, 2, r, lane - 1, sw);
-          stash_store<T, NC>(stash, 3, r, lane - 1, vh);
+          stash_store<T, NC>(stash, 0, lane - 1, r, su);
+          stash_store<T, NC>(stash, 1, lane - 1, r, sv);
+          stash_store<T, NC>(stash, 2, lane - 1, r, sw);
+          stash_store<T, NC>(stash, 3, lane - 1, r, sh);
         }
         continue;
       }
-      const int cc = r, i = i0 + cc;
-      const int j = j0 - 1 + lane;
-      if (lane >= 1 && lane <= kT2 && j < G.ny && HW_IN(i, G.nx, 9) && HW_IN(j, G.ny, 9)) {
+      // x pass: row r, lane l <-> tile column l - 1, and the stage update
+      const int i = i0 - 1 + lane, j = j0 + r;
+      if (lane >= 1 && lane <= kT2 && i < G.nx && HW_IN(i, G.nx, 9) && HW_IN(j, G.ny, 9)) {
         const long long p = (long long)j * G.nx + i;
-        T xu[NC], xv[NC], xw[NC], xh[NC], ubox[NC];
-        stash_load<T, NC>(stash, 0, lane - 1, cc, xu);
-        stash_load<T, NC>(stash, 1, lane - 1, cc, xv);
-        stash_load<T, NC>(stash, 2, lane - 1, cc, xw);
-        stash_load<T, NC>(stash, 3, lane - 1, cc, xh);
-        if (a.stage != 0) box_load<T, NC>(box, 0, (lane + 1) * kBP + cc + 2, 0, ubox);
+        T yu[NC], yv[NC], yw[NC], yh[NC], ubox[NC];
+        stash_load<T, NC>(stash, 0, r, lane - 1, yu);
+        stash_load<T, NC>(stash, 1, r, lane - 1, yv);
+        stash_load<T, NC>(stash, 2, r, lane - 1, yw);
+        stash_load<T, NC>(stash, 3, r, lane - 1, yh);
+        if (a.stage != 0) box_load<T, NC>(box, 0, (r + 2) * kBP + lane + 1, 0, ubox);
         T nu[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          const int kk = frame_comp<1, EQ>(k);
-          const T Lu = xu[k] - (Gu[kk] - Fu[kk]) * idy;
-          const T Lv = xv[k] - (Gw[kk] - Fw[kk]) * dxy;
-          const T Lw = xw[k] - (Gv[kk] - Fv[kk]);
-          const T vx = xh[k];
-          const T wyv = vh[kk];
+          const T Lu = yu[k] - (Gu[k] - Fu[k]) * idx;
+          const T Lv = yv[k] - (Gv[k] - Fv[k]);
+          const T Lw = yw[k] - (Gw[k] - Fw[k]) * dyx;
+          const T vx = vh[k];
+          const T wyv = yh[k];
           const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
           const long long hv = k * plane + p, hw_ = (NC + k) * plane + p;
           if (a.stage == 0) {
