@@ -55,10 +55,11 @@ MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.0  # executed, early-time 1536^2 state; dat
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
                 "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); FP64 flops "
                 "for the fp64 arm, FP32 flops of the fp32 kernel for the fp32 and fp32_ind64 arms")
-# DRAM bytes per cell of the stage kernel from the same captures (stage 1, 1536^2), scaled to
-# the bench grid by cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 651.9e6 / 1536 ** 2, "fp32": 337.2e6 / 1536 ** 2, "fp32_ind64": 343.7e6 / 1536 ** 2}
-TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 1536^2, scaled to the grid by cells"
+# DRAM bytes per cell of the stage kernel, mean of the three stage launches at 2048^2 (state
+# larger than L2; profiles/stage2d_euler_char_counters_1536.md), scaled to the bench grid by
+# cell count; None once the kernel has changed since the capture.
+TRAFFIC_PER_CELL = {"fp64": 268.8, "fp32": 129.44, "fp32_ind64": 134.49}
+TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 2048^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)
 # and write F; F = 12 stored fields, D = 8 limited derivatives -> (8F+D)/3 words.

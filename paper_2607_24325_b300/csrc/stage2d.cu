@@ -103,9 +103,10 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 // call rebuilds item j's stencil from the box (the owner's cell and
 // eigenvectors) and each owner collects its a_m by shuffle into a[k][m]
 // (0 on cleared lanes: the screen shows 1 + a_m = 1 there).  Runs between
-// rows, when little else is live.
+// rows; not inlined, which keeps its code out of the hot loop (fewer
+// instruction-fetch stalls) and its registers off the common path.
 template <int NC, bool CHR>
-__device__ __forceinline__ void pack64(const float* __restrict__ box, int bidx, int D, bool chr, float g,
+static __device__ __noinline__ void pack64(const float* __restrict__ box, int bidx, int D, bool chr, float g,
                                        unsigned pend, unsigned nqb, const WeightsT<double>& w64,
                                        volatile float (*a)[5]) {
   const int lane = threadIdx.x & 31;
@@ -507,12 +508,14 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         }
         continue;
       }
-      T Gu[NC], Gv[NC], Gw[NC];
+      // flux differences across the cell (high face, the next lane's low
+      // face, minus low face): the fluxes themselves are dead from here on
+      T dFu[NC], dFv[NC], dFw[NC];
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
-        Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
-        Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
-        Gw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1);
+        dFu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1) - Fu[k];
+        dFv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1) - Fv[k];
+        dFw[k] = __shfl_down_sync(HW_FULL_MASK, Fw[k], 1) - Fw[k];
       }
       if (it == 0) {  // y pass: column r, lane l <-> tile row l - 1; physical components
         if (lane >= 1 && lane <= kT2 && j0 - 1 + lane < G.ny) {
@@ -520,9 +523,9 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
 #pragma unroll
           for (int k = 0; k < NC; ++k) {
             const int kk = frame_comp<1, EQ>(k);
-            su[k] = -(Gu[kk] - Fu[kk]) * idy;
-            sv[k] = -(Gw[kk] - Fw[kk]) * dxy;
-            sw[k] = -(Gv[kk] - Fv[kk]);
+            su[k] = -dFu[kk] * idy;
+            sv[k] = -dFw[kk] * dxy;
+            sw[k] = -dFv[kk];
             sh[k] = vh[kk];
           }
           stash_store<T, NC>(stash, 0, lane - 1, r, su);
@@ -545,9 +548,9 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         T nu[NC];
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-          const T Lu = yu[k] - (Gu[k] - Fu[k]) * idx;
-          const T Lv = yv[k] - (Gv[k] - Fv[k]);
-          const T Lw = yw[k] - (Gw[k] - Fw[k]) * dyx;
+          const T Lu = yu[k] - dFu[k] * idx;
+          const T Lv = yv[k] - dFv[k];
+          const T Lw = yw[k] - dFw[k] * dyx;
           const T vx = vh[k];
           const T wyv = yh[k];
           const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
