@@ -6,7 +6,10 @@ Every .cu under csrc/ is compiled separately (in parallel) with
 spills, shared memory) is kept in ``_build/ptxas.log`` for inspection.
 ``build(checked=True)`` makes ``libhweno_checked.so`` from the same sources
 with ``-DHWENO_CHECKED`` (index checks in the stage kernels; see
-include/hweno_checked.h), in ``_build/checked``.
+include/hweno_checked.h), in ``_build/checked``; ``build(noscreen=True)``
+makes ``libhweno_noscreen.so`` with ``-DHWENO_SCREEN_OFF`` (the mixed
+precision's FP32 screen off: every lane takes the FP64 indicator), in
+``_build/noscreen``, for the test that the screen changes no output bit.
 """
 from __future__ import annotations
 
@@ -23,6 +26,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libhweno.so")
 LIB_CHECKED = os.path.join(PKG, "libhweno_checked.so")
+LIB_NOSCREEN = os.path.join(PKG, "libhweno_noscreen.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,15 +49,15 @@ def _stale(lib: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
-    lib = LIB_CHECKED if checked else LIB
-    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+def build(force: bool = False, verbose: bool = False, checked: bool = False, noscreen: bool = False) -> str:
+    lib = LIB_CHECKED if checked else (LIB_NOSCREEN if noscreen else LIB)
+    bdir = os.path.join(BUILD, "checked") if checked else (os.path.join(BUILD, "noscreen") if noscreen else BUILD)
     if not force and not _stale(lib):
         return lib
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-              "-Xptxas", "-v"] + (["-DHWENO_CHECKED"] if checked else [])
+              "-Xptxas", "-v"] + (["-DHWENO_CHECKED"] if checked else []) + (["-DHWENO_SCREEN_OFF"] if noscreen else [])
 
     def compile_one(src):
         obj = os.path.join(bdir, os.path.basename(src) + ".o")
@@ -80,4 +84,5 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False) -> 
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv)
+    build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv,
+          noscreen="--noscreen" in sys.argv)

@@ -17,9 +17,13 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 # HWENO_CHECKED=1 in the environment loads the index-checked build
-# (libhweno_checked.so: the same entry points plus include/hweno_checked.h's).
+# (libhweno_checked.so: the same entry points plus include/hweno_checked.h's);
+# HWENO_NOSCREEN=1 the build without the mixed precision's FP32 screen
+# (libhweno_noscreen.so, for the test that the screen changes no output bit).
 CHECKED = os.environ.get("HWENO_CHECKED") == "1"
-LIB_PATH = os.path.join(_HERE, "libhweno_checked.so" if CHECKED else "libhweno.so")
+NOSCREEN = os.environ.get("HWENO_NOSCREEN") == "1"
+LIB_PATH = os.path.join(_HERE, "libhweno_checked.so" if CHECKED else
+                        ("libhweno_noscreen.so" if NOSCREEN else "libhweno.so"))
 
 HWENO_OK, HWENO_ERR_ARG, HWENO_ERR_CUDA, HWENO_ERR_NONPHYSICAL = 0, 1, 2, 3
 HWENO_ERR_TIMEOUT, HWENO_ERR_OOM, HWENO_ERR_STATE = 4, 5, 6
