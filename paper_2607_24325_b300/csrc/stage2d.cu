@@ -418,50 +418,12 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
     const int D = 1 - it;
     if (it == 1) __syncthreads();  // the y pass's stash is complete
     const int lines = D == 0 ? G.ny - j0 : G.nx - i0;
-    // the warp's own rows r = warp + t nwarps first; mixed precision: a row
-    // the screen does not clear is listed (phase 0), and once every warp has
-    // listed its rows, the list is shared out: each listed row is screened
-    // again for its uncleared lanes (phase 1), its FP64 items packed and the
-    // row redone (phase 2)
-    const int own = (min(kT2, lines) - warp + nwarps - 1) / nwarps;
-    int t = 0, r = 0, e = warp, n_def = 0, phase = 0;
-    unsigned held = 0u;  // phase 2: the row's pending fields | this lane's uncleared ones << 4
+    // One warp row of the pass: reconstruction, fluxes, then the stash
+    // (first pass) or the stage update (second pass).  False, with the
+    // fields (*pend) and this lane's cells (*nqb) the screen did not clear,
+    // when the mixed precision defers the row.
     volatile float a64[W64 ? NC : 1][5];
-#pragma unroll 1
-    for (;;) {
-      unsigned redo = 0u;
-      if (phase == 0) {
-        if (t < own) {
-          r = warp + t * nwarps;
-          ++t;
-        } else {
-          if constexpr (!W64) {
-            break;
-          } else {
-            __syncthreads();  // every warp's deferred rows are listed
-            n_def = dl->n[D];
-            phase = 1;
-            continue;
-          }
-        }
-      } else if (phase == 1) {
-        if (e >= n_def) break;
-        r = HW_IN(e, kT2 + 2, 11) ? dl->row[e] : 0;
-        if (e < kDeferBal) {  // the listing warp's ballots: straight to the redo
-          unsigned pd = 0u, nb = 0u;
-#pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const unsigned b = dl->bal[e][k];
-            pd |= (b != 0u ? 1u : 0u) << k;
-            nb |= ((b >> lane) & 1u) << k;
-          }
-          redo = pd | (nb << 4);
-        }
-        e += nwarps;
-      } else {
-        redo = held;
-        phase = 1;
-      }
+    auto row = [&](const int r, const unsigned redo, unsigned& pend, unsigned& nqb) -> bool {
       // learned indicator: a warp whose 32 cells are all smooth takes p0
       bool lin = lin_all;
       if (smooth != nullptr && !lin) {
@@ -484,30 +446,10 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
           pack64<NC, CHR>(box, bidx, D, CHR && !lin, g, redo & 0xfu, redo >> 4, wp64, a64);
       }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
-      unsigned pend = 0u, nqb = 0u;
       if (!pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
                                    D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh,
-                                   redo & 0xfu, a64, &pend, &nqb)) {
-        if (phase == 0) {
-          int slot = 0;
-          if (lane == 0) {
-            slot = atomicAdd(&dl->n[D], 1);
-            if (HW_IN(slot, kT2 + 2, 10)) dl->row[slot] = (unsigned char)r;
-          }
-          slot = __shfl_sync(HW_FULL_MASK, slot, 0);
-          if (slot < kDeferBal) {
-#pragma unroll
-            for (int k = 0; k < NC; ++k) {
-              const unsigned b = __ballot_sync(HW_FULL_MASK, (nqb >> k) & 1u);
-              if (lane == 0) dl->bal[slot][k] = b;
-            }
-          }
-        } else {
-          held = pend | (nqb << 4);
-          phase = 2;
-        }
-        continue;
-      }
+                                   redo & 0xfu, a64, &pend, &nqb))
+        return false;
       // flux differences across the cell (high face, the next lane's low
       // face, minus low face): the fluxes themselves are dead from here on
       T dFu[NC], dFv[NC], dFw[NC];
@@ -533,7 +475,7 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
           stash_store<T, NC>(stash, 2, lane - 1, r, sw);
           stash_store<T, NC>(stash, 3, lane - 1, r, sh);
         }
-        continue;
+        return true;
       }
       // x pass: row r, lane l <-> tile column l - 1, and the stage update
       const int i = i0 - 1 + lane, j = j0 + r;
@@ -590,6 +532,59 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
             radx = fabs(a.adv_x);
             rady = fabs(a.adv_y);
           }
+        }
+      }
+      return true;
+    };
+    // the warp's own rows r = warp + t nwarps; mixed precision: a row the
+    // screen does not clear is listed, and once every warp has listed its
+    // rows the list is shared out: each listed row gets its uncleared lanes
+    // (from the listing warp's ballots, or by screening it again), its FP64
+    // items packed, and is redone.  Two loops, so that the common one holds
+    // none of the list's state.
+    const int own = (min(kT2, lines) - warp + nwarps - 1) / nwarps;
+#pragma unroll 1
+    for (int t = 0; t < own; ++t) {
+      const int r = warp + t * nwarps;
+      unsigned pend = 0u, nqb = 0u;
+      if (!row(r, 0u, pend, nqb)) {
+        if constexpr (W64) {
+          int slot = 0;
+          if (lane == 0) {
+            slot = atomicAdd(&dl->n[D], 1);
+            if (HW_IN(slot, kT2 + 2, 10)) dl->row[slot] = (unsigned char)r;
+          }
+          slot = __shfl_sync(HW_FULL_MASK, slot, 0);
+          if (slot < kDeferBal) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+              const unsigned b = __ballot_sync(HW_FULL_MASK, (nqb >> k) & 1u);
+              if (lane == 0) dl->bal[slot][k] = b;
+            }
+          }
+        }
+      }
+    }
+    if constexpr (W64) {
+      __syncthreads();  // every warp's deferred rows are listed
+      const int n_def = dl->n[D];
+#pragma unroll 1
+      for (int e = warp; e < n_def; e += nwarps) {
+        const int r = HW_IN(e, kT2 + 2, 11) ? dl->row[e] : 0;
+        unsigned redo = 0u;
+        if (e < kDeferBal) {  // the listing warp's ballots
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const unsigned b = dl->bal[e][k];
+            redo |= (b != 0u ? 1u : 0u) << k;
+            redo |= ((b >> lane) & 1u) << (4 + k);
+          }
+        }
+#pragma unroll 1
+        for (;;) {  // at most twice: screened again (no ballots kept), then redone
+          unsigned pend = 0u, nqb = 0u;
+          if (row(r, redo, pend, nqb)) break;
+          redo = pend | (nqb << 4);
         }
       }
     }
