@@ -51,14 +51,14 @@ ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64",
 # algorithmic FP32 flops are taken as the fp32 arm's (a lower bound on its
 # roofline fraction).
 FLOPS_PER_CELL_STAGE = {"fp64": 5550.0, "fp32": 5130.0, "fp32_ind64": 5130.0}
-MIXED_FP64_FLOPS_PER_CELL_STAGE = 13.0  # executed, early-time 1536^2 state; data dependent
+MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.3  # executed, early-time 1536^2 state; data dependent
 FLOPS_SOURCE = ("ncu executed FP op counts (2 per FMA) of the three stage launches at 1536^2, ring-lane "
                 "redundancy (52x32/1536) removed (profiles/stage2d_euler_char_counters_1536.md); FP64 flops "
                 "for the fp64 arm, FP32 flops of the fp32 kernel for the fp32 and fp32_ind64 arms")
 # DRAM bytes per cell of the stage kernel, mean of the three stage launches at 2048^2 (state
 # larger than L2; profiles/stage2d_euler_char_counters_1536.md), scaled to the bench grid by
 # cell count; None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 268.87, "fp32": 129.44, "fp32_ind64": 133.58}
+TRAFFIC_PER_CELL = {"fp64": 268.81, "fp32": 129.47, "fp32_ind64": 132.87}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 2048^2, scaled to the grid by cells"
 # Algorithmic HBM bytes per cell-stage: stage 1 reads F fields and writes
 # F + D, stages 2-3 read 2F (state in + base average/limited derivatives)

@@ -107,7 +107,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 // instruction-fetch stalls) and its registers off the common path.
 template <int NC, bool CHR>
 static __device__ __noinline__ void pack64(const float* __restrict__ box, int bidx, int D, bool chr, float g,
-                                       unsigned pend, unsigned nqb, const WeightsT<double>& w64,
+                                       unsigned pend, unsigned nqb, double eps, int pow2, int typical,
                                        volatile float (*a)[5]) {
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
@@ -157,7 +157,7 @@ static __device__ __noinline__ void pack64(const float* __restrict__ box, int bi
       for (int k = 1; k < NC; ++k) v = f == k ? x[k] : v;
       st.q[s] = v;
     }
-    const Weights5 r5 = indicator64(st, w64.eps, w64.pow2, w64.typical);
+    const Weights5 r5 = indicator64(st, eps, pow2, typical);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       if ((pend >> k) & 1u) {
@@ -443,7 +443,8 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
       }
       if constexpr (W64) {
         if (redo != 0u)
-          pack64<NC, CHR>(box, bidx, D, CHR && !lin, g, redo & 0xfu, redo >> 4, wp64, a64);
+          pack64<NC, CHR>(box, bidx, D, CHR && !lin, g, redo & 0xfu, redo >> 4, wx64.eps, wx64.pow2,
+                          wx64.typical, a64);
       }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
       if (!pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
