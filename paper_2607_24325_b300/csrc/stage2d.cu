@@ -104,7 +104,10 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 // eigenvectors) and each owner collects its a_m by shuffle into a[k][m]
 // (0 on cleared lanes: the screen shows 1 + a_m = 1 there).  Runs between
 // rows; not inlined, which keeps its code out of the hot loop (fewer
-// instruction-fetch stalls) and its registers off the common path.
+// instruction-fetch stalls) and its registers off the common path.  The
+// indicator's parameters (eps, the power, the form) come by value: a
+// reference to a weight set would give the caller's set an address in
+// local memory and keep all of it live through the row loop.
 template <int NC, bool CHR>
 static __device__ __noinline__ void pack64(const float* __restrict__ box, int bidx, int D, bool chr, float g,
                                        unsigned pend, unsigned nqb, double eps, int pow2, int typical,
