@@ -286,7 +286,8 @@ def _burgers2d(N, T, **kw):
 
 def test_2d_burgers_table_pins_weight_power(golden_dir):
     """With beta + eps the oracle reproduces the printed 2D Burgers row; the
-    printed 2D formula beta^2 + eps does not (reading recorded in the design doc)."""
+    printed 2D formula beta^2 + eps does not: the printed table fixes the
+    power of the 2D weights."""
     tab = _table(golden_dir)
     N, T = 40, 0.5 / math.pi
     ex = W.cells_2d(W.sine_burgers_2d(T), 0, 4, 0, 4, N, N)[0]
@@ -779,3 +780,73 @@ def test_dmr_initial_state_matches_fine_sampling():
     X, Y = np.meshgrid(xs, ys)
     fr = (X < 1.0 / 6.0 + Y / math.sqrt(3.0)).astype(float).reshape(ny, k, nx, k).mean(axis=(1, 3))
     assert np.abs(post[0] * fr + pre[0] * (1 - fr) - U[0]).max() < 1e-4
+
+
+# ------------------------------------------------------------ ghost layers
+def test_padded_state_1d_hand_written_ghosts():
+    """1D Euler, 3 cells.  Left side reflective: the ghost at -1 mirrors cell
+    0 and -2 mirrors cell 1, with the momentum and the moments of rho and E
+    negated (the x-derivative of an even quantity is odd under the mirror,
+    that of the odd momentum even).  Right side outflow: both ghosts copy
+    cell 2.  Then an inflow left side: the fixed state, zero moments."""
+    U = np.array([[1., 2., 3.], [4., 5., 6.], [7., 8., 9.],
+                  [10., 11., 12.], [13., 14., 15.], [16., 17., 18.]])
+    p = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=3,
+                       bc=(oracle.BC_REFLECT, oracle.BC_OUTFLOW, 0, 0))
+    P = oracle.padded_state(p, U)
+    expect = np.array([
+        [2., 1., 1., 2., 3., 3., 3.],
+        [-5., -4., 4., 5., 6., 6., 6.],
+        [8., 7., 7., 8., 9., 9., 9.],
+        [-11., -10., 10., 11., 12., 12., 12.],
+        [14., 13., 13., 14., 15., 15., 15.],
+        [-17., -16., 16., 17., 18., 18., 18.],
+    ])
+    assert np.array_equal(P, expect)
+    p2 = oracle.Problem(dim=1, equation=oracle.EQ_EULER, nx=3, bc=(oracle.BC_INFLOW, oracle.BC_PERIODIC, 0, 0),
+                        bc_state=[[0.5, 0.1, 2.0, 0.0], [0.0] * 4, [0.0] * 4, [0.0] * 4])
+    P2 = oracle.padded_state(p2, U)
+    assert np.array_equal(P2[:, :2], [[0.5, 0.5], [0.1, 0.1], [2.0, 2.0], [0, 0], [0, 0], [0, 0]])
+    # periodic right side: the ghosts at 3 and 4 are cells 0 and 1
+    assert np.array_equal(P2[:, 5:], U[:, :2])
+
+
+def test_padded_state_2d_hand_written_ghosts():
+    """2D Euler on 3 x 2 cells (fields rho, m_x, m_y, E; x-moments; y-moments).
+    Left outflow, right reflective, bottom inflow, top reflective.  The x
+    sides are filled on the interior rows first, then the y sides on every
+    column (which defines the corners)."""
+    nx, ny = 3, 2
+    U = np.zeros((12, ny, nx))
+    for f in range(12):
+        for j in range(ny):
+            for i in range(nx):
+                U[f, j, i] = 100 * f + 10 * j + i + 1
+    inflow = [1.5, 0.25, -0.5, 3.0]
+    p = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny,
+                       lin_w=(0.99, 0.0025, 0.0025, 0.0025, 0.0025),
+                       bc=(oracle.BC_OUTFLOW, oracle.BC_REFLECT, oracle.BC_INFLOW, oracle.BC_REFLECT),
+                       bc_state=[[0.0] * 4, [0.0] * 4, inflow, [0.0] * 4])
+    P = oracle.padded_state(p, U)
+    # mirror signs (field index d*4 + k).  Across an x face: m_x odd; the
+    # x-moments of rho, m_y, E odd; the y-moment of m_x odd.  Across a y face:
+    # m_y odd; the y-moments of rho, m_x, E odd; the x-moment of m_y odd.
+    sx = {0: 1, 1: -1, 2: 1, 3: 1, 4: -1, 5: 1, 6: -1, 7: -1, 8: 1, 9: -1, 10: 1, 11: 1}
+    sy = {0: 1, 1: 1, 2: -1, 3: 1, 4: 1, 5: 1, 6: -1, 7: 1, 8: -1, 9: -1, 10: 1, 11: -1}
+    E = np.full((12, ny + 4, nx + 4), np.nan)
+    E[:, 2:2 + ny, 2:2 + nx] = U
+    for j in range(ny):                       # x sides, interior rows
+        for f in range(12):
+            E[f, 2 + j, 0] = E[f, 2 + j, 1] = U[f, j, 0]                      # outflow
+            E[f, 2 + j, 2 + nx] = sx[f] * U[f, j, nx - 1]                     # mirror of the last cell
+            E[f, 2 + j, 3 + nx] = sx[f] * U[f, j, nx - 2]
+    for i in range(nx + 4):                   # y sides, every column
+        for f in range(12):
+            E[f, 0, i] = E[f, 1, i] = inflow[f] if f < 4 else 0.0             # inflow
+            E[f, 2 + ny, i] = sy[f] * E[f, 1 + ny, i]                          # mirror of the top row
+            E[f, 3 + ny, i] = sy[f] * E[f, ny, i]
+    assert np.array_equal(P, E)
+    # spot values written out: rho above the top-right corner cell, and the
+    # y-moment of m_x in the right ghost column of row 0
+    assert P[0, 2 + ny, 2 + nx] == U[0, ny - 1, nx - 1]  # rho: even under both mirrors
+    assert P[9, 2, 2 + nx] == -U[9, 0, nx - 1]
