@@ -56,6 +56,22 @@ Layout layout(long long n, int nc, size_t esz, int ntasks) {
   return L;
 }
 
+Layout layout_for(long long n, int nc, size_t esz) {
+  return layout(n, nc, esz, (int)((n + hw::kTile1 - 1) / hw::kTile1));
+}
+
+// The largest cell count whose layout fits the scratch array (the layout's
+// size grows with n, so a bisection finds it exactly).
+long long max_cells(int nc, size_t esz) {
+  long long lo = 0, hi = (long long)(kScratchBytes / esz) + 1;  // layout(lo) fits, layout(hi) does not
+  while (hi - lo > 1) {
+    const long long mid = lo + (hi - lo) / 2;
+    if (layout_for(mid, nc, esz).total <= kScratchBytes) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // Writes the instance descriptor and the control block (next-alpha slot
 // zeroed) and the warp-task table of this call into the scratch array.
 __global__ void k_noalloc_setup(hw::Inst1 inst, hw::Ctl ctl, hw::Inst1* inst_out, hw::Ctl* ctl_out,
@@ -89,8 +105,7 @@ extern "C" hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const voi
     snprintf(msg, sizeof msg,
              "nx = %lld needs %zu bytes of step scratch; the allocation-free step is limited to %zu bytes "
              "(%lld cells for this equation and precision)",
-             n, L.total, kScratchBytes,
-             (long long)((kScratchBytes - 4 * kAlign) / ((5 * nc) * esz + sizeof(int2) / hw::kTile1 + 1)));
+             n, L.total, kScratchBytes, max_cells(nc, esz));
     return hw::report_error(HWENO_ERR_ARG, msg);
   }
   int dev = 0;
@@ -167,6 +182,8 @@ extern "C" hweno_status hweno_step_1d_noalloc(const hweno_config* cfg, const voi
     a.stage = s;
     a.gamma_gas = cfg->gamma_gas;
     a.adv = cfg->adv_x;
+    a.gammaf = (float)cfg->gamma_gas;  // the FP32 kernels read these copies
+    a.advf = (float)cfg->adv_x;
     a.wp = wp;
     e = hw::launch_stage1d(cfg->precision, cfg->equation, cfg->charwise, a, sms, stream);
     if (e != cudaSuccess) return hw::report_error(HWENO_ERR_CUDA, cudaGetErrorString(e));

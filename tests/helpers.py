@@ -20,13 +20,24 @@ def cfg_from(prob: oracle.Problem, precision: int = hw.FP64) -> hw.Config:
 
 
 def plane_rel_err(got, ref) -> float:
-    """max over field planes of max|got - ref| / (max|ref| of that plane)."""
+    """max over field planes of max|got - ref| / (max|ref| of that plane).
+
+    A non-finite value in `got` where `ref` is finite (or a NaN anywhere in
+    the difference) counts as an infinite error, so a NaN never compares as
+    "close": Python's max() would otherwise drop it."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
+    if got.shape != ref.shape:
+        raise ValueError(f"shape mismatch {got.shape} vs {ref.shape}")
+    if not np.all(np.isfinite(got) | ~np.isfinite(ref)):
+        return float("inf")
     worst = 0.0
     for f in range(ref.shape[0]):
         scale = np.abs(ref[f]).max() + 1e-300
-        worst = max(worst, float(np.abs(got[f] - ref[f]).max() / scale))
+        e = float(np.abs(got[f] - ref[f]).max() / scale)
+        if not np.isfinite(e):
+            return float("inf")
+        worst = max(worst, e)
     return worst
 
 
@@ -50,9 +61,16 @@ def oracle_spread(prob, U, ax, ay=0.0, rel=2.0 ** -53, samples=4, seed=0):
 
 
 def plane_errs(got, ref):
+    """Per-plane relative errors; a plane holding a NaN or an infinity that
+    the reference does not have gets an infinite error."""
     got = np.asarray(got, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
-    return np.array([np.abs(got[f] - ref[f]).max() / (np.abs(ref[f]).max() + 1e-300) for f in range(ref.shape[0])])
+    out = []
+    for f in range(ref.shape[0]):
+        bad = ~np.isfinite(got[f]) & np.isfinite(ref[f])
+        e = np.abs(got[f] - ref[f]).max() / (np.abs(ref[f]).max() + 1e-300)
+        out.append(np.inf if bad.any() or not np.isfinite(e) else e)
+    return np.array(out)
 
 
 def within_spread(got, ref, spread, floor, factor=100.0):
