@@ -20,7 +20,7 @@
  * integrals of monomials + a dense linear solve), so that the printed
  * appendix tables can pin this code from outside.
  *
- * Readings of points the paper leaves open (all listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - 1D beta is sum_l (l! c_l)^2 (the printed formula drops the square).
  *   - 2D p0 fits the derivative moments of the 4 face neighbours in the
  *     least-squares sense (this is exactly what Appendix A prints).
