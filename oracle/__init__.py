@@ -157,6 +157,8 @@ def lib():
         L.or_euler_eigen.argtypes = [C.c_int, C.c_int, dp, C.c_double, dp, dp]
         L.or_weight_deviation.argtypes = [pp, dp, dp]
         L.or_padded_state.argtypes = [pp, dp, dp]
+        L.or_flop_count.argtypes = [C.c_int]
+        L.or_flop_count.restype = C.c_longlong
         _lib = L
     return _lib
 
@@ -284,3 +286,9 @@ def padded_state(prob: Problem, U) -> np.ndarray:
     if lib().or_padded_state(C.byref(ps), _ptr(U), _ptr(out)):
         raise RuntimeError("or_padded_state failed")
     return out
+
+
+def flop_count(reset: bool = False) -> int:
+    """The oracle's running count of the method's flops (plain evaluation of
+    each formula, charged for the grid's own cells and faces)."""
+    return int(lib().or_flop_count(1 if reset else 0))

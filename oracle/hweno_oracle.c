@@ -43,6 +43,50 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
+/* Flop counter: the method's arithmetic per cell and stage.                */
+/* ------------------------------------------------------------------------ */
+/* Every formula of Steps 1-4 (and of Remark 1's projections) is charged as
+ * its plain evaluation, whatever way this file happens to compute it:
+ *  - add, subtract, multiply, divide and square root cost 1; absolute
+ *    values, comparisons and negations cost nothing;
+ *  - a product with a constant (a coefficient of the maps, a basis value at
+ *    a fixed point, a factorial, a Gauss weight, a linear weight, gamma, the
+ *    grid spacings, alpha, dt) costs 1, a constant 0 removes the term and a
+ *    constant +-1 makes the product free;
+ *  - a sum of k terms costs k - 1;
+ *  - a quantity used several times is formed once per cell (primitive
+ *    variables, eigenvector matrices, 1/gamma_0) or once per face state;
+ *  - only the grid's own cells and faces are charged: one reconstruction of
+ *    each cell per stage (per pass for characteristic 2D Euler, where a pass
+ *    needs only its own two faces and one limited derivative), and its right
+ *    (and top) face.  Work this file does beyond that -- the ring of cells
+ *    outside the grid, the other two faces of a characteristic pass, L by
+ *    elimination instead of its closed form, primitive variables recomputed
+ *    -- is not charged.
+ * or_flop_count reads the running total. */
+static long long g_flops = 0;
+static int g_charge = 1; /* 0 while reconstructing cells outside the grid */
+#define FL(n) (g_flops += g_charge ? (long long)(n) : 0LL)
+
+long long or_flop_count(int reset) {
+  const long long v = g_flops;
+  if (reset) g_flops = 0;
+  return v;
+}
+
+/* flops of sum_k c[k] x[k] for constants c[0..n-1] (stride apart) */
+static int fl_dot(const double* c, int n, int stride) {
+  int terms = 0, muls = 0;
+  for (int k = 0; k < n; ++k) {
+    const double v = c[k * stride];
+    if (v == 0.0) continue;
+    ++terms;
+    if (v != 1.0 && v != -1.0) ++muls;
+  }
+  return terms > 0 ? muls + terms - 1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Dense linear algebra: Gaussian elimination with partial pivoting.        */
 /* Solves A X = B; A is n x n, B is n x m, both row-major; B becomes X.     */
 /* ------------------------------------------------------------------------ */
@@ -238,6 +282,9 @@ static void nonlinear_weights(const or_problem* p, int nlin, const double* beta,
     for (int m = 0; m < np; ++m) w[m] = p->lin_w[m];
     return;
   }
+  /* tau: nlin differences, nlin - 1 adds, one product; tau^2; per weight
+   * (beta^2), + eps, the quotient, 1 +, gamma x; the sum; np quotients */
+  FL(2 * nlin + 1 + np * (4 + (p->weight_pow == 2)) + nlin + np);
   double tau = 0.0;
   for (int m = 1; m < np; ++m) tau += fabs(beta[0] - beta[m]);
   tau /= nlin;
@@ -257,15 +304,18 @@ int or_recon_cell_1d(const or_problem* p, const double* in, double dx, double* o
   build_maps();
   /* Step 1 */
   const double d[5] = {in[0], in[1], in[2], dx * in[3], dx * in[4]};
+  FL(2);
   double c0[5], c1[2], c2[2];
   for (int l = 0; l < 5; ++l) {
     double s = 0.0;
     for (int k = 0; k < 5; ++k) s += G0_1D[l * 5 + k] * d[k];
     c0[l] = s;
+    FL(fl_dot(G0_1D + l * 5, 5, 1));
   }
   for (int l = 0; l < 2; ++l) {
     c1[l] = G1_1D[l * 2 + 0] * in[0] + G1_1D[l * 2 + 1] * in[1];
     c2[l] = G2_1D[l * 2 + 0] * in[1] + G2_1D[l * 2 + 1] * in[2];
+    FL(fl_dot(G1_1D + l * 2, 2, 1) + fl_dot(G2_1D + l * 2, 2, 1));
   }
   /* Step 2: beta = sum_{l>=1} (l! c_l)^2 */
   double beta[3] = {0.0, c1[1] * c1[1], c2[1] * c2[1]};
@@ -274,6 +324,13 @@ int or_recon_cell_1d(const or_problem* p, const double* in, double dx, double* o
     beta[0] = beta_typical_1d(c0, 5);
     beta[1] = beta_typical_1d(c1, 2);
     beta[2] = beta_typical_1d(c2, 2);
+    /* the closed quadratic forms: the quartic's 6 terms (c1^2 with a unit
+     * coefficient: 1 product, the others 2) and 5 adds; c^2 for a line */
+    FL(16 + 1 + 1);
+  } else {
+    /* beta_1, beta_2: a square each; beta_0: c_1^2 and (l! c_l)^2 for
+     * l = 2..4 (2 products each), 3 adds */
+    FL(2 + 7 + 3);
   }
   /* Step 3: weights and Eq. (hweno-reconstruction-1D) */
   double w[3];
@@ -286,6 +343,10 @@ int or_recon_cell_1d(const or_problem* p, const double* in, double dx, double* o
     q0 /= g0;
     cu[l] = w[0] * q0 + (l < 2 ? w[1] * c1[l] + w[2] * c2[l] : 0.0);
   }
+  /* Eq. (hweno-reconstruction-1D): for l < 2 two products and two
+   * subtractions, the quotient by gamma_0, three products and two adds; for
+   * l >= 2 the quotient and one product */
+  FL(2 * 10 + 3 * 2);
   double uL = 0.0, uR = 0.0, dL = 0.0, dR = 0.0;
   for (int l = 0; l < 5; ++l) {
     uL += cu[l] * pw(-0.5, l);
@@ -295,6 +356,9 @@ int or_recon_cell_1d(const or_problem* p, const double* in, double dx, double* o
       dR += l * cu[l] * pw(0.5, l - 1) / dx;
     }
   }
+  /* u at the faces: 5 terms, 4 non-unit basis values; u': 4 terms, each
+   * with its constant l (+-1/2)^(l-1) / dx; v-hat: a difference and 1/dx */
+  FL(2 * 8 + 2 * 7 + 2);
   out[0] = uL;
   out[1] = uR;
   out[2] = dL;
@@ -335,7 +399,34 @@ static double beta_typical_2d(const double* c) {
   return b;
 }
 
-int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy, double* out) {
+/* flops of one face's values: u at the 3 Gauss points (basis values
+ * phi_l(xi, eta) there), u_xi and u_eta (their derivatives, each sum then
+ * divided by the spacing); face 0/1 at xi = -+1/2, 2/3 at eta = -+1/2 */
+static int fl_face_2d(int face) {
+  int n = 0;
+  for (int mu = 0; mu < 3; ++mu) {
+    double xi, eta;
+    if (face < 2) { xi = face == 0 ? -0.5 : 0.5; eta = GAUSS_S[mu]; }
+    else { xi = GAUSS_S[mu]; eta = face == 2 ? -0.5 : 0.5; }
+    for (int t = 0; t < 3; ++t) {
+      double b[15];
+      for (int l = 0; l < 15; ++l) {
+        const int m = EXP2[l][0], k = EXP2[l][1];
+        const int dm = t == 1, dk = t == 2;
+        if (m < dm || k < dk) { b[l] = 0.0; continue; }
+        b[l] = (dm ? m : 1) * (dk ? k : 1) * pw(xi, m - dm) * pw(eta, k - dk);
+      }
+      n += fl_dot(b, 15, 1) + (t > 0); /* the derivatives: / dx or / dy */
+    }
+  }
+  return n;
+}
+
+/* Sec. 2.2 Steps 1-3 for one field; all four faces and both limited
+ * derivatives are evaluated, the flop counter is charged for the faces in
+ * `need` (bit f: face f; bit 4: v-hat; bit 5: w-hat). */
+static void recon_cell_2d(const or_problem* p, const double* q, double dx, double dy, double* out,
+                          unsigned need) {
   build_maps();
   /* Step 1 */
   double c0[15], cm[4][3];
@@ -343,13 +434,16 @@ int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy,
     double s = 0.0;
     for (int k = 0; k < 17; ++k) s += G0_2D[l * 17 + k] * q[k];
     c0[l] = s;
+    FL(fl_dot(G0_2D + l * 17, 17, 1));
   }
   for (int m = 0; m < 4; ++m) {
     double a[3];
     for (int r = 0; r < 3; ++r) a[r] = q[(SOFF[m][r][1] + 1) * 3 + (SOFF[m][r][0] + 1)];
-    for (int l = 0; l < 3; ++l)
+    for (int l = 0; l < 3; ++l) {
       cm[m][l] = GM_2D[9 * m + l * 3 + 0] * a[0] + GM_2D[9 * m + l * 3 + 1] * a[1] +
                  GM_2D[9 * m + l * 3 + 2] * a[2];
+      FL(fl_dot(GM_2D + 9 * m + l * 3, 3, 1));
+    }
   }
   /* Step 2: beta = sum over non-constant terms of (m! n! c)^2 */
   double beta[5];
@@ -365,6 +459,14 @@ int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy,
       const double lin[15] = {cm[m][0], cm[m][1], cm[m][2]};
       beta[m + 1] = beta_typical_2d(lin);
     }
+    /* the quartic's closed quadratic form: 29 terms (c_1^2 and c_2^2 with
+     * unit coefficients: 1 product, the others 2), 28 adds; c_1^2 + c_2^2
+     * for each linear polynomial */
+    FL(84 + 4 * 3);
+  } else {
+    /* beta_0: 14 squares, 11 of them after a factorial product (m! n! > 1),
+     * 13 adds; beta_m: two squares and an add */
+    FL(38 + 4 * 3);
   }
   /* Step 3: weights and Eq. (hweno-reconstruction-2D) */
   double w[5];
@@ -375,6 +477,23 @@ int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy,
     if (l < 3)
       for (int m = 0; m < 4; ++m) { q0 -= p->lin_w[m + 1] * cm[m][l]; lin += w[m + 1] * cm[m][l]; }
     cu[l] = w[0] * q0 / p->lin_w[0] + lin;
+  }
+  /* Eq. (hweno-reconstruction-2D): for l < 3 four products and subtractions
+   * for p0 - sum gamma_m p_m, four products and three adds for sum omega_m
+   * p_m, omega_0 (.) / gamma_0 and the add; for l >= 3 omega_0 c / gamma_0 */
+  FL(3 * (8 + 7 + 2 + 1) + 12 * 2);
+  for (int f = 0; f < 4; ++f)
+    if (need & (1u << f)) FL(fl_face_2d(f));
+  /* v-hat, w-hat: the terms of cu with a nonzero cell integral of d/dxi
+   * (d/deta) of their basis function */
+  {
+    double bv[15], bw[15];
+    for (int l = 0; l < 15; ++l) {
+      bv[l] = mono_dif(0, EXP2[l][0]) * mono_avg(0, EXP2[l][1]);
+      bw[l] = mono_avg(0, EXP2[l][0]) * mono_dif(0, EXP2[l][1]);
+    }
+    if (need & 16u) FL(fl_dot(bv, 15, 1));
+    if (need & 32u) FL(fl_dot(bw, 15, 1));
   }
   /* point values at the Gauss points of the four faces */
   for (int face = 0; face < 4; ++face)
@@ -397,6 +516,10 @@ int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy,
   out[36] = vh;
   out[37] = wh;
   for (int m = 0; m < 5; ++m) { out[38 + m] = w[m]; out[43 + m] = beta[m]; }
+}
+
+int or_recon_cell_2d(const or_problem* p, const double* q, double dx, double dy, double* out) {
+  recon_cell_2d(p, q, dx, dy, out, 63u);
   return 0;
 }
 
@@ -632,6 +755,10 @@ static void cell_recon_1d(const or_problem* p, padded_t* P, int i, double dx, re
   double Wm[4], W0[4], Wp[4], Zm[4], Zp[4];
   if (chr) {
     or_euler_eigen(1, 0, U0, p->gamma_gas, R, L);
+    /* Remark 1: primitive variables of the cell average (11), the entries of
+     * R (6) and of L in closed form (16); L times 5 stencil vectors (9
+     * products, 6 adds each) */
+    FL(11 + 6 + 16 + 5 * 15);
     matvec(nc, L, Um, Wm); matvec(nc, L, U0, W0); matvec(nc, L, Up, Wp);
     matvec(nc, L, Vm, Zm); matvec(nc, L, Vp, Zp);
   } else {
@@ -646,6 +773,8 @@ static void cell_recon_1d(const or_problem* p, padded_t* P, int i, double dx, re
     for (int t = 0; t < 5; ++t) o[t][k] = out[t];
   }
   if (chr) {
+    /* R (first row ones) times 5 vectors: 2 + 5 + 5 flops each */
+    FL(5 * 12);
     matvec(nc, R, o[0], rec->uL); matvec(nc, R, o[1], rec->uR);
     matvec(nc, R, o[2], rec->dL); matvec(nc, R, o[3], rec->dR);
     matvec(nc, R, o[4], rec->vh);
@@ -677,7 +806,7 @@ static void cell_recon_2d(const or_problem* p, padded_t* P, int i, int j, double
   if (!chr) {
     for (int k = 0; k < nc; ++k) {
       double out[48];
-      or_recon_cell_2d(p, q[k], dx, dy, out);
+      recon_cell_2d(p, q[k], dx, dy, out, 63u);
       for (int face = 0; face < 4; ++face)
         for (int mu = 0; mu < 3; ++mu)
           for (int t = 0; t < 3; ++t) rec->fv[face][mu][t][k] = out[(face * 3 + mu) * 3 + t];
@@ -688,10 +817,15 @@ static void cell_recon_2d(const or_problem* p, padded_t* P, int i, int j, double
   }
   double U0[4];
   for (int k = 0; k < nc; ++k) U0[k] = q[k][4];
+  FL(14); /* primitive variables of the cell average, once for both passes */
   /* pass dir 0 gives the x faces and v-hat, pass dir 1 the y faces and w-hat */
   for (int dir = 0; dir < 2; ++dir) {
     double R[16], L[16];
     or_euler_eigen(2, dir, U0, p->gamma_gas, R, L);
+    /* Remark 1: the entries of R (6) and of L in closed form (18); L (two
+     * structural zeros and a one in the shear row) times the 17 stencil
+     * vectors, 23 flops each */
+    FL(6 + 18 + 17 * 23);
     double w[4][17];
     for (int s = 0; s < 17; ++s) {
       double x[4], y[4];
@@ -700,7 +834,10 @@ static void cell_recon_2d(const or_problem* p, padded_t* P, int i, int j, double
       for (int k = 0; k < nc; ++k) w[k][s] = y[k];
     }
     double out[4][48];
-    for (int k = 0; k < nc; ++k) or_recon_cell_2d(p, w[k], dx, dy, out[k]);
+    for (int k = 0; k < nc; ++k) recon_cell_2d(p, w[k], dx, dy, out[k], (3u << (2 * dir)) | (16u << dir));
+    /* R (two structural zeros, four ones) times the pass's 18 face values and
+     * its limited derivative, 20 flops each */
+    FL(19 * 20);
     for (int face = 2 * dir; face < 2 * dir + 2; ++face)
       for (int mu = 0; mu < 3; ++mu)
         for (int t = 0; t < 3; ++t) {
@@ -735,6 +872,24 @@ static void lf_flux(const or_problem* p, int dir, double a, const double* um, co
   }
 }
 
+/* flops of the global LF fluxes at one 1D face or one 2D Gauss point, from
+ * the two face states: per state the physical flux and the derivative
+ * fluxes f'(u) v (and f'(u) w), each component of each family
+ * 1/2 (F- + F+) - (alpha/2) (u+ - u-) for 5.
+ *   advection: a u, a v (, a w);  Burgers: u^2 / 2 (2), u v (, u w);
+ *   1D Euler per state: u, p, E + p, H (7), F (2), the Jacobian's entries (9),
+ *     f'(u) v (10: first row a copy, the others 3 products and 2 adds);
+ *   2D Euler per state: u, v, q^2, p, E + p, H (11), F (4), the entries of
+ *     A_x or A_y (12), A v and A w (19 each: 0 + 7 + 5 + 7). */
+static int fl_flux_point(const or_problem* p) {
+  const int fam = p->dim + 1, nc = or_ncomp(p);
+  int per_state;
+  if (p->equation == OR_EQ_ADVECTION) per_state = fam;
+  else if (p->equation == OR_EQ_BURGERS) per_state = 2 + (fam - 1);
+  else per_state = p->dim == 1 ? 7 + 2 + 9 + 10 : 11 + 4 + 12 + 2 * 19;
+  return 2 * per_state + 5 * fam * nc;
+}
+
 /* ------------------------------------------------------------------------ */
 /* The spatial operator.                                                    */
 /* ------------------------------------------------------------------------ */
@@ -747,13 +902,19 @@ static int operator_1d(const or_problem* p, const double* U, double ax, double* 
   double* Fu = (double*)malloc(sizeof(double) * 4 * (nx + 1));
   double* Fv = (double*)malloc(sizeof(double) * 4 * (nx + 1));
   if (!rec || !Fu || !Fv) { free(rec); free(Fu); free(Fv); free(P.a); return -1; }
-  for (int i = -1; i <= nx; ++i) cell_recon_1d(p, &P, i, dx, &rec[i + 1]);
+  for (int i = -1; i <= nx; ++i) {
+    g_charge = i >= 0 && i < nx; /* the ring cells are not the grid's own */
+    cell_recon_1d(p, &P, i, dx, &rec[i + 1]);
+    g_charge = 1;
+  }
   /* face i+1/2 for i = -1..nx-1 stored at index i+1 */
   for (int i = -1; i < nx; ++i) {
     const rec1_t* a = &rec[i + 1];
     const rec1_t* b = &rec[i + 2];
     lf_flux(p, 0, ax, a->uR, b->uL, a->dR, b->dL, Fu + 4 * (i + 1), Fv + 4 * (i + 1));
+    if (i >= 0) FL(fl_flux_point(p)); /* each cell's right face */
   }
+  FL((long long)nx * 2 * nc * 2); /* L = -(F_right - F_left) / dx per field */
   for (int i = 0; i < nx; ++i)
     for (int k = 0; k < nc; ++k) {
       Lo[(size_t)k * nx + i] = -(Fu[4 * (i + 1) + k] - Fu[4 * i + k]) / dx;
@@ -781,14 +942,20 @@ static int operator_2d(const or_problem* p, const double* U, double ax, double a
     for (int i = -1; i <= nx; ++i) {
       const int in_x = i >= 0 && i < nx, in_y = j >= 0 && j < ny;
       if (!in_x && !in_y) continue; /* corners are never needed */
+      g_charge = in_x && in_y;       /* the ring cells are not the grid's own */
       cell_recon_2d(p, &P, i, j, dx, dy, &REC(i, j));
+      g_charge = 1;
     }
+  /* per face: the Gauss points' fluxes and the Gauss sums (3 products and 2
+   * adds per quantity); only each cell's right and top face is charged */
+  const int fl_face = 3 * fl_flux_point(p) + 3 * nc * 5;
   /* x faces: f-hat_{i+1/2,j} = dy sum_mu sigma_mu f-hat(u-, u+) */
   for (int j = 0; j < ny; ++j)
     for (int i = -1; i < nx; ++i) {
       const rec2_t* a = &REC(i, j);
       const rec2_t* b = &REC(i + 1, j);
       double* o = FX + ((size_t)j * (nx + 1) + (i + 1)) * 12;
+      if (i >= 0) FL(fl_face);
       for (int mu = 0; mu < 3; ++mu) {
         double fu[4], fv[4], fw[4];
         lf_flux(p, 0, ax, a->fv[1][mu][0], b->fv[0][mu][0], a->fv[1][mu][1], b->fv[0][mu][1], fu, fv);
@@ -806,6 +973,7 @@ static int operator_2d(const or_problem* p, const double* U, double ax, double a
       const rec2_t* a = &REC(i, j);
       const rec2_t* b = &REC(i, j + 1);
       double* o = FY + ((size_t)(j + 1) * nx + i) * 12;
+      if (j >= 0) FL(fl_face);
       for (int mu = 0; mu < 3; ++mu) {
         double gu[4], gv[4], gw[4];
         lf_flux(p, 1, ay, a->fv[3][mu][0], b->fv[2][mu][0], a->fv[3][mu][1], b->fv[2][mu][1], gu, gv);
@@ -818,6 +986,7 @@ static int operator_2d(const or_problem* p, const double* U, double ax, double a
       }
     }
   const size_t plane = (size_t)nx * ny;
+  FL((long long)nx * ny * 3 * nc * 4); /* -(x_r - x_l + y_r - y_l) / h per field */
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < nx; ++i) {
       const double* xl = FX + ((size_t)j * (nx + 1) + i) * 12;
@@ -862,6 +1031,8 @@ int or_alpha(const or_problem* p, const double* U, double* ax, double* ay) {
   const int nc = or_ncomp(p), ny = p->dim == 2 ? p->ny : 1;
   const size_t plane = (size_t)p->nx * ny;
   double mx = 0.0, my = 0.0;
+  /* Euler: u (, v), p, c and |u| + c (, |v| + c) per cell; scalars: none */
+  if (p->equation == OR_EQ_EULER) FL((long long)plane * (p->dim == 1 ? 10 : 14));
   for (size_t c = 0; c < plane; ++c) {
     double s[4];
     for (int k = 0; k < nc; ++k) s[k] = U[k * plane + c];
@@ -906,16 +1077,19 @@ int or_step(const or_problem* p, double* U, double dt, double ax, double ay) {
   or_problem ps = *p;
   /* stage 1: u(1) = u-hat^n + dt L(u^n) */
   if (or_operator(&ps, U0, ax, ay, L, H0)) goto done;
+  FL((long long)nall * 2); /* u-hat + dt L per stored field */
   for (size_t c = 0; c < nu; ++c) Us[c] = U0[c] + dt * L[c];
   for (size_t c = 0; c < nd; ++c) Us[nu + c] = H0[c] + dt * L[nu + c];
   /* stage 2: u(2) = 3/4 u-hat^n + 1/4 (u-hat(1) + dt L(u(1))) */
   ps.t = p->t + dt;
   if (or_operator(&ps, Us, ax, ay, L, Hs)) goto done;
+  FL((long long)nall * 5); /* 3/4 u-hat^n + 1/4 (u-hat + dt L) */
   for (size_t c = 0; c < nu; ++c) Us[c] = 0.75 * U0[c] + 0.25 * (Us[c] + dt * L[c]);
   for (size_t c = 0; c < nd; ++c) Us[nu + c] = 0.75 * H0[c] + 0.25 * (Hs[c] + dt * L[nu + c]);
   /* stage 3: u^{n+1} = 1/3 u-hat^n + 2/3 (u-hat(2) + dt L(u(2))) */
   ps.t = p->t + 0.5 * dt;
   if (or_operator(&ps, Us, ax, ay, L, Hs)) goto done;
+  FL((long long)nall * 5); /* 1/3 u-hat^n + 2/3 (u-hat + dt L) */
   for (size_t c = 0; c < nu; ++c) U[c] = U0[c] / 3.0 + 2.0 / 3.0 * (Us[c] + dt * L[c]);
   for (size_t c = 0; c < nd; ++c) U[nu + c] = H0[c] / 3.0 + 2.0 / 3.0 * (Hs[c] + dt * L[nu + c]);
   rc = 0;

@@ -111,6 +111,11 @@ int or_step(const or_problem* p, double* U, double dt, double ax, double ay);
 int or_run(const or_problem* p, double* U, double t_final, int max_steps,
            double* t_out, int* steps_out);
 
+/* Running count of the method's flops (see the counting rules at the top of
+ * hweno_oracle.c): the plain evaluation of each formula, charged for the
+ * grid's own cells and faces only.  reset != 0 zeroes it after reading. */
+long long or_flop_count(int reset);
+
 /* Learned troubled-cell indicator (not in the paper).  dev[cell] = the
  * largest |omega_m / gamma_m - 1| of the plain scheme's nonlinear weights
  * over every reconstructed field (both passes for 2D characteristic Euler):

@@ -14,6 +14,7 @@ precision's FP32 screen off: every lane takes the FP64 indicator), in
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -41,23 +42,41 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(lib: str) -> bool:
+def _fingerprint(flags: list[str]) -> str:
+    """Hash of every source and header and of the compiler flags: a library
+    is rebuilt whenever it was built from different contents (file times
+    alone miss an edit made while a build was running)."""
+    h = hashlib.sha256(" ".join(flags).encode())
+    deps = sorted([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+                  [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)])
+    for d in deps:
+        if os.path.isfile(d):
+            h.update(os.path.basename(d).encode())
+            with open(d, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def _stale(lib: str, fingerprint: str) -> bool:
     if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(lib)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
-    return any(os.path.getmtime(d) > t for d in deps)
+    try:
+        with open(lib + ".stamp") as fh:
+            return fh.read().strip() != fingerprint
+    except OSError:
+        return True
 
 
 def build(force: bool = False, verbose: bool = False, checked: bool = False, noscreen: bool = False) -> str:
     lib = LIB_CHECKED if checked else (LIB_NOSCREEN if noscreen else LIB)
     bdir = os.path.join(BUILD, "checked") if checked else (os.path.join(BUILD, "noscreen") if noscreen else BUILD)
-    if not force and not _stale(lib):
+    common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+              "-Xptxas", "-v"] + (["-DHWENO_CHECKED"] if checked else []) + (["-DHWENO_SCREEN_OFF"] if noscreen else [])
+    fp = _fingerprint(common)  # taken before compiling: an edit during the build makes the next call rebuild
+    if not force and not _stale(lib, fp):
         return lib
     os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
-              "-Xptxas", "-v"] + (["-DHWENO_CHECKED"] if checked else []) + (["-DHWENO_SCREEN_OFF"] if noscreen else [])
 
     def compile_one(src):
         obj = os.path.join(bdir, os.path.basename(src) + ".o")
@@ -78,6 +97,8 @@ def build(force: bool = False, verbose: bool = False, checked: bool = False, nos
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")
     os.replace(tmp, lib)
+    with open(lib + ".stamp", "w") as fh:
+        fh.write(fp + "\n")
     if verbose:
         print(f"built {lib}", file=sys.stderr)
     return lib

@@ -324,6 +324,26 @@ def test_2d_euler_smooth_converges_fifth_order():
     assert math.log(errs[0] / errs[1]) / math.log(2) > 4.5
 
 
+def test_2d_euler_table_magnitude_40(golden_dir):
+    """The printed 2D Euler row at 40^2 (Example 4, T = 2): L1 and Linf of the
+    density within 1.3x.  The run takes dt = CFL dx / alpha at CFL 0.3: the
+    RK3 time error (proportional to dt^3) is then an eighth of that at CFL 0.6,
+    where it is as large as the spatial error at this grid; the printed row is
+    the spatial error of the characteristic-wise reconstruction (Remark 1)."""
+    tab = _table(golden_dir)
+    N, T = 40, 2.0
+    p = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=N, ny=N, xlo=0, xhi=2, ylo=0, yhi=2,
+                       lin_w=W2D, cfl=0.3)
+    U0 = W.cells_2d(W.euler_smooth_2d(0.0), 0, 2, 0, 2, N, N)
+    ex = W.cells_2d(W.euler_smooth_2d(T), 0, 2, 0, 2, N, N)[0]
+    U, t, _ = oracle.run(p, U0, T)
+    assert t == T
+    e = np.abs(U[0] - ex)
+    pl1, pli = tab[("euler2d", N)]
+    assert pl1 / 1.3 < e.mean() < 1.3 * pl1, (e.mean(), pl1)
+    assert pli / 1.3 < e.max() < 1.3 * pli, (e.max(), pli)
+
+
 # ----------------------------------------------- invariants and symmetries
 def test_conservation_periodic_through_shocks():
     N = 64

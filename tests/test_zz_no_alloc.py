@@ -67,7 +67,8 @@ def test_noalloc_step_matches_regular_step_twice(eq, charwise, n, prec):
     tol = 1e-12 if prec == hw.FP64 else 1e-6
     # two calls in a row: the second starts from the first one's output
     U_dev = torch.from_numpy(U0).to(dtype).cuda().contiguous()
-    steps = [(1e-3, 2.5), (7e-4, 3.0)]
+    dx = 2.0 / n
+    steps = [(0.3 * dx / 2.5, 2.5), (0.25 * dx / 3.0, 3.0)]  # CFL 0.3 and 0.25
     ref = U0.astype(np.float64 if prec == hw.FP64 else np.float32)
     ref_or = U0.astype(np.float64)
     for dt, alpha in steps:
@@ -80,6 +81,7 @@ def test_noalloc_step_matches_regular_step_twice(eq, charwise, n, prec):
         assert plane_rel_err(got, ref) <= tol
         if prec == hw.FP64:
             ref_or = oracle.step(prob, ref_or, dt, alpha)
+            assert np.isfinite(ref_or).all()
             assert plane_rel_err(got, ref_or) <= 1e-12
         U_dev = out
 
@@ -97,13 +99,15 @@ def test_noalloc_step_in_place(eq, prec):
     U = torch.from_numpy(U0).to(dtype).cuda().contiguous()
     ref_or = U0.astype(np.float64)
     ref = U0.astype(np.float64 if prec == hw.FP64 else np.float32)
-    for dt, alpha in [(1e-3, 2.5), (8e-4, 2.8)]:
+    dx = 2.0 / n
+    for dt, alpha in [(0.3 * dx / 2.5, 2.5), (0.25 * dx / 2.8, 2.8)]:
         hw.hweno_step_1d_noalloc(cfg, U, U, dt, alpha)
         torch.cuda.synchronize()
         got = U.cpu().numpy()
         assert np.isfinite(got).all()
         ref = _regular_step(cfg, np.ascontiguousarray(ref), dt, alpha)
         ref_or = oracle.step(prob, ref_or, dt, alpha)
+        assert np.isfinite(ref_or).all()
         if prec == hw.FP64:
             assert plane_rel_err(got, ref_or) <= 1e-12
             assert plane_rel_err(got, ref) <= 1e-12
