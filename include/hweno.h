@@ -186,6 +186,29 @@ hweno_status hweno_apply_operator(hweno_solver* s, double alpha_x, double alpha_
  * from the solver's current time, which it advances by dt. */
 hweno_status hweno_step(hweno_solver* s, double dt, double alpha_x, double alpha_y);
 
+/* One RK stage (1, 2 or 3) of an SSP-RK3 step (Step 4 of Sec. 2.2) with the
+ * given dt and Lax-Friedrichs constants, for single 2D solvers: the stages
+ * of hweno_step one call at a time, so that a caller can replace rows of a
+ * stage's output (hweno_rows) before the next stage reads them -- the halo
+ * exchange of a grid split into slabs of rows.  Stage 1 reads the state and
+ * writes the stage-1 buffer (and the limited derivatives of Step 3), stage 2
+ * reads it and writes the stage-2 buffer, stage 3 reads that and writes the
+ * state, moves the solver's time by dt and recomputes alpha.  The stages of
+ * one step run in order with the same dt and alpha (else HWENO_ERR_STATE or
+ * HWENO_ERR_ARG). */
+hweno_status hweno_stage(hweno_solver* s, int stage, double dt, double alpha_x, double alpha_y);
+
+/* Copy rows [row0, row0 + nrows) of every field plane of one of the solver's
+ * buffers -- 0: the state, 1: the stage-1 output, 2: the stage-2 output --
+ * to (to_solver = 0) or from (to_solver = 1) the caller's device buffer
+ * `rows`, laid out [nf][nrows][nx] in the solver's element type.  Single 2D
+ * solvers; ordered on the solver's stream after earlier calls. */
+hweno_status hweno_rows(hweno_solver* s, int buffer, int row0, int nrows, void* rows, int to_solver);
+
+/* Recompute alpha from the current state's cell averages (after hweno_rows
+ * replaced some of them) and return it, as hweno_alpha.  Synchronises. */
+hweno_status hweno_alpha_update(hweno_solver* s, double* alpha_x, double* alpha_y);
+
 /* Advance to t_final with the device-resident CFL time step (alpha from the
  * averages at the start of each step, last step clipped to t_final), at most
  * max_steps steps.  Steps are replayed from a captured CUDA graph; the host
@@ -259,6 +282,11 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
                                  double* t_out, int* steps_out);
 /* The autotuner of hweno_autotune for a batch (all instances at once). */
 hweno_status hweno_batch_autotune(hweno_batch* b, int reps, double* best_ms, int* shape_out);
+/* hweno_set_profiling / hweno_profile for a batch: the stage kernels'
+ * device time over all instances (one launch per stage covers the batch). */
+hweno_status hweno_batch_set_profiling(hweno_batch* b, int enable);
+hweno_status hweno_batch_profile(hweno_batch* b, double* stage_ms, long long* stage_launches,
+                                 long long* kernel_launches);
 /* Apply the operator to every instance with per-instance Lax-Friedrichs
  * constants (host array): alpha[n] for 1D, alpha[n][2] = (alpha_x, alpha_y)
  * for 2D; L_out [nf][total], dhat_out [nc*dim][total] (device buffers; a 2D

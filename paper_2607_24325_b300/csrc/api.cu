@@ -175,6 +175,10 @@ struct Engine {
   unsigned char* troubled = nullptr;  // network output per cell
   unsigned char* smooth = nullptr;    // dilated complement: 1 = linear path
   float z_thresh = 0.f;
+  // hweno_stage: the stage that ran last (0: none pending) and its step's
+  // dt, alpha and start time
+  int stage_done = 0;
+  double st_dt = 0.0, st_ax = 0.0, st_ay = 0.0, st_t0 = 0.0;
 
   ~Engine() {
     for (cudaEvent_t e : pev) cudaEventDestroy(e);
@@ -546,6 +550,78 @@ struct Engine {
     return leave();
   }
 
+  // One RK stage of a step with given dt and alpha (hweno_stage): stage 1
+  // reads S and writes A (and the limited derivatives H), stage 2 reads A and
+  // writes B, stage 3 reads B and writes S and moves the time by dt.
+  hweno_status stage_manual(int s, double dt, double ax, double ay) {
+    if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
+    if (dim != 2 || batch2) return fail(HWENO_ERR_ARG, "hweno_stage serves single 2D solvers");
+    if (s < 1 || s > 3) return fail(HWENO_ERR_ARG, "stage must be 1, 2 or 3");
+    if (!(dt >= 0.0) || !std::isfinite(dt) || !(ax >= 0.0) || !(ay >= 0.0) || !std::isfinite(ax) ||
+        !std::isfinite(ay))
+      return fail(HWENO_ERR_ARG, "dt and alpha must be finite and non-negative");
+    if (s != stage_done + 1) return fail(HWENO_ERR_STATE, "stage %d follows stage %d: stages run 1, 2, 3", s,
+                                         stage_done);
+    if (s > 1 && (dt != st_dt || ax != st_ax || ay != st_ay))
+      return fail(HWENO_ERR_ARG, "the three stages of a step take the same dt and alpha");
+    HW_TRY(enter());
+    if (s == 1) {
+      HW_TRY(read_ctl());
+      st_t0 = ctl_host[0].t;
+      st_dt = dt;
+      st_ax = ax;
+      st_ay = ay;
+      if (learned) HW_TRY(run_indicator());
+      hw::Ctl c = ctl_init[0];
+      c.t = st_t0;
+      c.dt = dt;
+      c.ax = ax;
+      c.ay = ay;
+      c.dtf = (float)dt;
+      c.axf = (float)ax;
+      c.ayf = (float)ay;
+      c.done = 0;
+      ctl_host[0] = c;
+      HW_CK(cudaMemcpyAsync(ctl_manual, ctl_host, sizeof(hw::Ctl), cudaMemcpyHostToDevice, own));
+      HW_CK(cudaStreamSynchronize(own));
+    }
+    const void* in = s == 1 ? S : (s == 2 ? A : B);
+    void* out = s == 1 ? A : (s == 2 ? B : S);
+    HW_TRY(timed_stage(s, in, out, ctl_manual));
+    stage_done = s == 3 ? 0 : s;
+    if (s == 3) {
+      // the solver's time moves by dt; alpha of the new state (hweno_alpha_update
+      // again once rows of it have been replaced)
+      HW_TRY(read_ctl());
+      if (prof) HW_TRY(collect_prof());
+      ctl_host[0].t = st_t0 + dt;
+      HW_CK(cudaMemcpyAsync(ctl, ctl_host, sizeof(hw::Ctl), cudaMemcpyHostToDevice, own));
+      HW_TRY(alpha_init());
+    }
+    return leave();
+  }
+
+  // Rows [row0, row0 + nrows) of every field plane of buffer `which` (0: the
+  // state S, 1: stage-1 output A, 2: stage-2 output B) to or from a device
+  // buffer laid out [nf][nrows][nx].
+  hweno_status rows(int which, int row0, int nrows, void* buf, int to_solver) {
+    if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
+    if (dim != 2 || batch2) return fail(HWENO_ERR_ARG, "hweno_rows serves single 2D solvers");
+    if (which < 0 || which > 2) return fail(HWENO_ERR_ARG, "buffer must be 0 (state), 1 or 2 (stage outputs)");
+    if (!buf) return fail(HWENO_ERR_ARG, "row buffer is NULL");
+    if (row0 < 0 || nrows < 1 || row0 + nrows > cfg.ny)
+      return fail(HWENO_ERR_ARG, "rows [%d, %d) lie outside [0, %d)", row0, row0 + nrows, cfg.ny);
+    HW_TRY(enter());
+    char* base = static_cast<char*>(which == 0 ? S : (which == 1 ? A : B));
+    const size_t width = (size_t)nrows * cfg.nx * esz, plane = (size_t)cells * esz;
+    char* p = base + (size_t)row0 * cfg.nx * esz;
+    if (to_solver)
+      HW_CK(cudaMemcpy2DAsync(p, plane, buf, width, width, nf, cudaMemcpyDeviceToDevice, own));
+    else
+      HW_CK(cudaMemcpy2DAsync(buf, width, p, plane, width, nf, cudaMemcpyDeviceToDevice, own));
+    return leave();
+  }
+
   hweno_status apply_operator(const double* ax, double ay, void* L, void* dh) {
     if (!has_state) return fail(HWENO_ERR_STATE, "no state set");
     if (!L || !dh) return fail(HWENO_ERR_ARG, "output pointer is NULL");
@@ -755,6 +831,25 @@ hweno_status hweno_step(hweno_solver* s, double dt, double alpha_x, double alpha
   return s->e.manual_step(dt, alpha_x, alpha_y);
 }
 
+hweno_status hweno_stage(hweno_solver* s, int stage, double dt, double alpha_x, double alpha_y) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  return s->e.stage_manual(stage, dt, alpha_x, alpha_y);
+}
+
+hweno_status hweno_rows(hweno_solver* s, int buffer, int row0, int nrows, void* rows, int to_solver) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  return s->e.rows(buffer, row0, nrows, rows, to_solver);
+}
+
+hweno_status hweno_alpha_update(hweno_solver* s, double* alpha_x, double* alpha_y) {
+  if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
+  if (!s->e.has_state) return fail(HWENO_ERR_STATE, "no state set");
+  HW_TRY(s->e.enter());
+  HW_TRY(s->e.alpha_init());
+  HW_TRY(s->e.leave());
+  return hweno_alpha(s, alpha_x, alpha_y);
+}
+
 hweno_status hweno_advance(hweno_solver* s, double t_final, int max_steps, double* t_out,
                            int* steps_out) {
   if (!s) return fail(HWENO_ERR_ARG, "solver is NULL");
@@ -833,6 +928,20 @@ hweno_status hweno_batch_advance(hweno_batch* b, const double* t_final, int max_
     if (steps_out) steps_out[k] = b->e.ctl_host[k].steps;
   }
   return st;
+}
+
+hweno_status hweno_batch_set_profiling(hweno_batch* b, int enable) {
+  if (!b) return fail(HWENO_ERR_ARG, "batch is NULL");
+  return b->e.set_profiling(enable);
+}
+
+hweno_status hweno_batch_profile(hweno_batch* b, double* stage_ms, long long* stage_launches,
+                                 long long* kernel_launches) {
+  if (!b) return fail(HWENO_ERR_ARG, "batch is NULL");
+  if (stage_ms) *stage_ms = b->e.prof_stage_ms;
+  if (stage_launches) *stage_launches = b->e.prof_stage_launches;
+  if (kernel_launches) *kernel_launches = b->e.prof_launches;
+  return HWENO_OK;
 }
 
 hweno_status hweno_batch_apply_operator(hweno_batch* b, const double* alpha, void* L_out,

@@ -42,6 +42,7 @@ EXPORTS = (
     "hweno_batch_create", "hweno_batch_destroy",
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
     "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
+    "hweno_batch_set_profiling", "hweno_batch_profile", "hweno_stage", "hweno_rows", "hweno_alpha_update",
     "hweno_indicator_features", "hweno_indicator_labels", "hweno_indicator_load", "hweno_indicator_off",
     "hweno_indicator_mask", "hweno_mlp_create", "hweno_mlp_destroy", "hweno_mlp_set_params",
     "hweno_mlp_get_params", "hweno_mlp_gradient", "hweno_mlp_train_step", "hweno_mlp_mean_loss",
@@ -174,6 +175,12 @@ def load():
     L.hweno_batch_advance.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int)]
     L.hweno_batch_apply_operator.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
+    L.hweno_batch_set_profiling.argtypes = [vp, C.c_int]
+    L.hweno_stage.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double]
+    L.hweno_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_int]
+    L.hweno_alpha_update.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.hweno_batch_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_longlong)]
     L.hweno_step_1d_noalloc.argtypes = [cp, vp, vp, C.c_double, C.c_double, vp]
     fp, ip = C.POINTER(C.c_float), C.POINTER(C.c_int)
     L.hweno_indicator_features.argtypes = [vp, vp]
@@ -282,6 +289,32 @@ def hweno_set_profiling(h, enable: bool):
 def hweno_profile(h):
     ms, n, k = C.c_double(), C.c_longlong(), C.c_longlong()
     _check(load().hweno_profile(h, C.byref(ms), C.byref(n), C.byref(k)))
+    return ms.value, n.value, k.value
+
+
+def hweno_stage(h, stage: int, dt: float, alpha_x: float, alpha_y: float = 0.0):
+    _check(load().hweno_stage(h, int(stage), dt, alpha_x, alpha_y))
+
+
+def hweno_rows(h, buffer: int, row0: int, rows, to_solver: bool):
+    """rows: a CUDA tensor [nf, nrows, nx] of the solver's element type."""
+    nrows = int(rows.shape[1])
+    _check(load().hweno_rows(h, int(buffer), int(row0), nrows, C.c_void_p(_buf(rows)[0]), 1 if to_solver else 0))
+
+
+def hweno_alpha_update(h):
+    ax, ay = C.c_double(), C.c_double()
+    _check(load().hweno_alpha_update(h, C.byref(ax), C.byref(ay)))
+    return ax.value, ay.value
+
+
+def hweno_batch_set_profiling(h, enable: bool):
+    _check(load().hweno_batch_set_profiling(h, 1 if enable else 0))
+
+
+def hweno_batch_profile(h):
+    ms, n, k = C.c_double(), C.c_longlong(), C.c_longlong()
+    _check(load().hweno_batch_profile(h, C.byref(ms), C.byref(n), C.byref(k)))
     return ms.value, n.value, k.value
 
 
@@ -626,6 +659,13 @@ class Batch:
         if np.isscalar(t_final):
             t_final = [t_final] * self.n
         return hweno_batch_advance(self.h, t_final, max_steps)
+
+    def set_profiling(self, enable: bool = True):
+        hweno_batch_set_profiling(self.h, enable)
+
+    def profile(self):
+        """(summed stage-kernel ms, stage launches, kernels launched by advance)."""
+        return hweno_batch_profile(self.h)
 
     def apply_operator(self, alpha):
         """alpha: per instance alpha (1D) or (alpha_x, alpha_y) pairs (2D)."""

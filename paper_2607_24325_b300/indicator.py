@@ -30,8 +30,8 @@ def shock_entropy_config(n: int, precision: int = hw.FP64) -> hw.Config:
 
 def shock_entropy_problem(seed: int, n: int, precision: int = hw.FP64):
     """(config, initial state) of one member of the family; the shock sits on
-    the face x = 0.2 (n a multiple of 5)."""
-    f = W.shock_entropy_2d(seed=seed)
+    the cell face nearest x = 0.2 (exactly 0.2 when n is a multiple of 5)."""
+    f = W.shock_entropy_2d(seed=seed, x_shock=round(0.2 * n) / n)
     prm = f.params
     cfg = shock_entropy_config(n, precision)
     post = W.prim_to_cons_2d(prm["rho2"], prm["u2"], 0.0, prm["p2"])

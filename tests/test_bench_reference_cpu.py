@@ -21,7 +21,7 @@ def test_reference_arm_line():
     import bench
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
-    assert d["config"] == bench.headline_config(bench.N_GRID, 1, "fp32_ind64")
+    assert d["config"] == bench.headline_config(bench.N_GRID, 1, "fp64")
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
     cb = d["cpu_baseline"]
