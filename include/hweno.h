@@ -347,6 +347,37 @@ hweno_status hweno_mlp_mean_loss(hweno_mlp* m, double* loss);
 /* FP32 probabilities prob[n] (device) of n samples feat[n][75] (device). */
 hweno_status hweno_mlp_predict(hweno_mlp* m, const float* feat, long long n, float* prob);
 
+/* The whole training of the indicator's network in one call (the loop of
+ * hweno_mlp_train_step, on the GPU; the paper's own weights define the
+ * labels: Sec. 2.2 Step 3).  feat [n][75] and dev [n] are device float
+ * arrays (features and label sources of hweno_indicator_features /
+ * hweno_indicator_labels; a cell is a positive when dev > delta).  Each
+ * epoch visits the n samples in a seeded random order, minibatches of
+ * `batch` (a trailing partial batch is skipped), one Adam step each; the
+ * order of epoch e is the Fisher-Yates shuffle of 0..n-1 driven by SplitMix64
+ * from the state seed + (e + 1) * 0xD1B54A32D192ED03 (index j = next() mod
+ * (i + 1) for i = n-1 down to 1; hweno_train_permutation writes it).
+ * pos_weight <= 0 takes min(50, max(1, negatives / positives)), counted on
+ * the device.  init_params (host float[3521]) or, when NULL, seeded
+ * He-normal hidden layers, N(0, 1/32) output weights and zero biases.
+ * params_out (host float[3521]) receives the trained parameters, losses_out
+ * (host double[epochs], may be NULL) each epoch's mean minibatch loss.
+ * Allocates its work buffers and frees them before returning; runs on
+ * cuda_stream and synchronises it. */
+typedef struct {
+  int epochs;                 /* passes over the data, >= 1 */
+  int batch;                  /* minibatch size, 1 <= batch <= min(n, 2^24) */
+  double lr;                  /* Adam step size, > 0 */
+  double delta;               /* label threshold on max |omega_m / gamma_m - 1| */
+  double pos_weight;          /* class weight of positives; <= 0: from the labels */
+  unsigned long long seed;    /* permutations (and the default initialisation) */
+} hweno_train_opts;
+hweno_status hweno_indicator_train(const float* feat, const float* dev, long long n, const hweno_train_opts* opts,
+                                   const float* init_params, float* params_out, double* losses_out,
+                                   void* cuda_stream);
+/* The visiting order of epoch `epoch` of hweno_indicator_train (host int[n]). */
+void hweno_train_permutation(unsigned long long seed, int epoch, long long n, int* perm);
+
 /* ---- Allocation-free step (the paper has no counterpart: this serves
  * callers that cannot allocate device memory when they need a step, e.g. a
  * host that has given the whole device memory budget to its own pool

@@ -7,7 +7,9 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -158,6 +160,7 @@ struct Engine {
   hw::Inst2* inst2_d = nullptr;
   hw::Tile2* tiles2_d = nullptr;
   long long ntiles2 = 0;
+  unsigned* sched_d = nullptr;   // the 2D stage kernel's tile scheduler (2 words, self-resetting)
   hw::WeightParams wp{};
   cudaGraphExec_t gexec = nullptr;
   bool has_state = false;
@@ -185,7 +188,7 @@ struct Engine {
     if (gexec) cudaGraphExecDestroy(gexec);
     cudaFree(S); cudaFree(A); cudaFree(B); cudaFree(H);
     cudaFree(ctl); cudaFree(ctl_manual); cudaFree(inst_d); cudaFree(tasks_d); cudaFree(alpha_op);
-    cudaFree(inst2_d); cudaFree(tiles2_d);
+    cudaFree(inst2_d); cudaFree(tiles2_d); cudaFree(sched_d);
     cudaFree(mlp_w); cudaFree(mlp_bias); cudaFree(troubled); cudaFree(smooth);
     if (ctl_host) cudaFreeHost(ctl_host);
     if (ev) cudaEventDestroy(ev);
@@ -299,6 +302,8 @@ struct Engine {
     HW_CK(cudaMalloc(&ctl, sizeof(hw::Ctl) * n));
     HW_CK(cudaMalloc(&ctl_manual, sizeof(hw::Ctl) * n));
     HW_CK(cudaMalloc(&alpha_op, sizeof(double) * 2 * n));
+    HW_CK(cudaMalloc(&sched_d, sizeof(unsigned) * 2));
+    HW_CK(cudaMemset(sched_d, 0, sizeof(unsigned) * 2));
     HW_CK(cudaMallocHost(&ctl_host, sizeof(hw::Ctl) * n));
     HW_CK(cudaMemcpy(ctl, ctl_init.data(), sizeof(hw::Ctl) * n, cudaMemcpyHostToDevice));
     HW_CK(cudaMemcpy(ctl_manual, ctl_init.data(), sizeof(hw::Ctl) * n, cudaMemcpyHostToDevice));
@@ -337,6 +342,7 @@ struct Engine {
       a.f32 = hw::stage2_f32(grid, ax, ay, cfg.gamma_gas, cfg.adv_x, cfg.adv_y);
       a.plane = cells;
       a.smooth = learned && s > 0 ? smooth : nullptr;
+      a.sched = sched_d;
       if (batch2) {
         a.batched = 1;
         a.inst = inst2_d;
@@ -1100,6 +1106,106 @@ hweno_status hweno_mlp_mean_loss(hweno_mlp* m, double* loss) {
   HW_CK(cudaStreamSynchronize(m->stream));
   *loss = acc[1] > 0.f ? acc[0] / acc[1] : 0.0;
   return HWENO_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood, 2014): the generator of the training
+// permutations and of the default initialisation.
+static unsigned long long splitmix64(unsigned long long& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  unsigned long long z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void hweno_train_permutation(unsigned long long seed, int epoch, long long n, int* perm) {
+  unsigned long long st = seed + (unsigned long long)(epoch + 1) * 0xD1B54A32D192ED03ull;
+  for (long long i = 0; i < n; ++i) perm[i] = (int)i;
+  for (long long i = n - 1; i > 0; --i) {
+    const long long j = (long long)(splitmix64(st) % (unsigned long long)(i + 1));
+    const int t = perm[i];
+    perm[i] = perm[j];
+    perm[j] = t;
+  }
+}
+
+hweno_status hweno_indicator_train(const float* feat, const float* dev, long long n, const hweno_train_opts* o,
+                                   const float* init_params, float* params_out, double* losses_out,
+                                   void* cuda_stream) {
+  if (!feat || !dev || !o || !params_out) return fail(HWENO_ERR_ARG, "NULL argument");
+  if (n < 1 || n > INT32_MAX) return fail(HWENO_ERR_ARG, "n must lie in [1, 2^31)");
+  if (o->epochs < 1 || o->batch < 1 || o->batch > n || o->batch > (1 << 24))
+    return fail(HWENO_ERR_ARG, "need epochs >= 1 and 1 <= batch <= min(n, 2^24)");
+  if (!(o->lr > 0.0) || !std::isfinite(o->lr) || !std::isfinite(o->delta))
+    return fail(HWENO_ERR_ARG, "lr must be positive and delta finite");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int devno = 0, sms = 148;
+  HW_CK(cudaGetDevice(&devno));
+  HW_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devno));
+  // class weight of the positives
+  double pw = o->pos_weight;
+  unsigned long long* cnt = nullptr;
+  int* perm_d = nullptr;
+  hweno_mlp* m = nullptr;
+  hweno_status rc = HWENO_OK;
+  std::vector<int> perm((size_t)n);
+  std::vector<float> theta(hw::kMlpParams);
+  {
+    cudaError_t e = cudaMalloc(&cnt, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&perm_d, sizeof(int) * (size_t)n);
+    if (e == cudaSuccess) e = hw::launch_count_above(dev, n, (float)o->delta, cnt, sms, st);
+    unsigned long long pos = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&pos, cnt, sizeof pos, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      rc = fail(e == cudaErrorMemoryAllocation ? HWENO_ERR_OOM : HWENO_ERR_CUDA, "%s", cudaGetErrorString(e));
+      goto done;
+    }
+    if (!(pw > 0.0)) {
+      const double frac = (double)pos / (double)n;
+      pw = std::min(50.0, std::max(1.0, (1.0 - frac) / std::max(frac, 1e-6)));
+    }
+  }
+  if (init_params) {
+    std::copy(init_params, init_params + hw::kMlpParams, theta.begin());
+  } else {
+    // He-normal hidden layers, N(0, 1/32) output layer, zero biases; normal
+    // deviates by the Box-Muller transform of SplitMix64 uniforms
+    unsigned long long stt = o->seed;
+    auto normal = [&stt]() {
+      const double u1 = ((splitmix64(stt) >> 11) + 1.0) * 0x1p-53, u2 = (splitmix64(stt) >> 11) * 0x1p-53;
+      return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+    };
+    std::fill(theta.begin(), theta.end(), 0.0f);
+    for (int k = 0; k < 32 * 75; ++k) theta[k] = (float)(normal() * std::sqrt(2.0 / 75.0));
+    const int ow2 = 32 * 75 + 32, ow3 = ow2 + 32 * 32 + 32;
+    for (int k = 0; k < 32 * 32; ++k) theta[ow2 + k] = (float)(normal() * std::sqrt(2.0 / 32.0));
+    for (int k = 0; k < 32; ++k) theta[ow3 + k] = (float)(normal() * std::sqrt(1.0 / 32.0));
+  }
+  rc = hweno_mlp_create(o->batch, cuda_stream, &m);
+  if (rc != HWENO_OK) goto done;
+  rc = hweno_mlp_set_params(m, theta.data());
+  if (rc != HWENO_OK) goto done;
+  for (int ep = 0; ep < o->epochs; ++ep) {
+    hweno_train_permutation(o->seed, ep, n, perm.data());
+    cudaError_t e = cudaMemcpyAsync(perm_d, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { rc = fail(HWENO_ERR_CUDA, "%s", cudaGetErrorString(e)); goto done; }
+    for (long long b0 = 0; b0 + o->batch <= n; b0 += o->batch) {
+      rc = hweno_mlp_train_step(m, feat, dev, perm_d + b0, o->batch, o->delta, pw, o->lr);
+      if (rc != HWENO_OK) goto done;
+    }
+    double loss = 0.0;
+    rc = hweno_mlp_mean_loss(m, &loss);
+    if (rc != HWENO_OK) goto done;
+    if (losses_out) losses_out[ep] = loss;
+  }
+  rc = hweno_mlp_get_params(m, params_out);
+done:
+  if (m) hweno_mlp_destroy(m);
+  cudaFree(cnt);
+  cudaFree(perm_d);
+  return rc;
 }
 
 hweno_status hweno_mlp_predict(hweno_mlp* m, const float* feat, long long n, float* prob) {

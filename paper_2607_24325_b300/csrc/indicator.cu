@@ -483,6 +483,25 @@ cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* g, fl
   return cudaGetLastError();
 }
 
+// Number of label sources above delta (the positives of a training set):
+// a warp count per block, one atomic per warp.
+__global__ void __launch_bounds__(256) k_count_above(const float* __restrict__ dev, long long n, float delta,
+                                                     unsigned long long* count) {
+  unsigned c = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c += dev[i] > delta ? 1u : 0u;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(HW_FULL_MASK, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+cudaError_t launch_count_above(const float* dev, long long n, float delta, unsigned long long* count, int num_sms,
+                               cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_count_above<<<grid_for(n, 256, num_sms, 4), 256, 0, st>>>(dev, n, delta, count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_mlp_predict(const float* theta, const float* feat, long long N, float* prob, int num_sms,
                                cudaStream_t st) {
   k_mlp_predict<<<grid_for(N, 128, num_sms, 8), 128, 0, st>>>(theta, feat, N, prob);

@@ -69,6 +69,11 @@ struct Stage2Args {
   const Tile2* tiles;
   long long ntiles;
   const double* alpha_op;
+  // Dynamic tile scheduler of the persistent launch (nullptr: static
+  // stride): sched[0] hands out the tiles after each CTA's first, sched[1]
+  // counts finished CTAs; the last CTA to finish zeroes both, so every
+  // launch starts from zero.
+  unsigned* sched;
 };
 
 // Learned troubled-cell indicator: per-sample training buffers and the
@@ -116,6 +121,8 @@ cudaError_t launch_mlp_train(const float* theta, const float* feat, const float*
                              float delta, float pos_weight, MlpWork& w, float* grad, cudaStream_t st);
 cudaError_t launch_mlp_adam(float* theta, float* m, float* v, const float* g, float lr, int t, cudaStream_t st);
 cudaError_t launch_mlp_predict(const float* theta, const float* feat, long long N, float* prob, int num_sms,
+                               cudaStream_t st);
+cudaError_t launch_count_above(const float* dev, long long n, float delta, unsigned long long* count, int num_sms,
                                cudaStream_t st);
 cudaError_t prepare_mlp_infer2d();
 cudaError_t launch_mlp_infer2d(int precision, int equation, const void* U, const Grid2& G, long long plane,

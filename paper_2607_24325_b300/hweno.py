@@ -43,6 +43,7 @@ EXPORTS = (
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
     "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
     "hweno_batch_set_profiling", "hweno_batch_profile", "hweno_stage", "hweno_rows", "hweno_alpha_update",
+    "hweno_indicator_train", "hweno_train_permutation",
     "hweno_indicator_features", "hweno_indicator_labels", "hweno_indicator_load", "hweno_indicator_off",
     "hweno_indicator_mask", "hweno_mlp_create", "hweno_mlp_destroy", "hweno_mlp_set_params",
     "hweno_mlp_get_params", "hweno_mlp_gradient", "hweno_mlp_train_step", "hweno_mlp_mean_loss",
@@ -50,6 +51,11 @@ EXPORTS = (
     "hweno_get_time", "hweno_set_time",
 )
 MLP_NPARAM = 3521
+
+
+class hweno_train_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_double), ("delta", C.c_double),
+                ("pos_weight", C.c_double), ("seed", C.c_ulonglong)]
 
 
 class hweno_config(C.Structure):
@@ -177,6 +183,10 @@ def load():
     L.hweno_batch_apply_operator.argtypes = [vp, C.POINTER(C.c_double), vp, vp]
     L.hweno_batch_set_profiling.argtypes = [vp, C.c_int]
     L.hweno_stage.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double]
+    L.hweno_indicator_train.argtypes = [vp, vp, C.c_longlong, C.POINTER(hweno_train_opts), C.POINTER(C.c_float),
+                                        C.POINTER(C.c_float), C.POINTER(C.c_double), vp]
+    L.hweno_train_permutation.argtypes = [C.c_ulonglong, C.c_int, C.c_longlong, C.POINTER(C.c_int)]
+    L.hweno_train_permutation.restype = None
     L.hweno_rows.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, C.c_int]
     L.hweno_alpha_update.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.hweno_batch_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
@@ -427,6 +437,30 @@ def hweno_indicator_mask(h, smooth_out=None, troubled_out=None):
     ps = C.c_void_p(_buf(smooth_out)[0]) if smooth_out is not None else None
     pt = C.c_void_p(_buf(troubled_out)[0]) if troubled_out is not None else None
     _check(load().hweno_indicator_mask(h, ps, pt))
+
+
+def hweno_indicator_train(feat, dev, epochs, batch, lr, delta, pos_weight=0.0, seed=0, init_params=None,
+                          stream=None):
+    """The whole GPU training (see include/hweno.h); returns (parameters
+    float32[3521], per-epoch mean losses)."""
+    n = int(dev.numel())
+    o = hweno_train_opts(int(epochs), int(batch), float(lr), float(delta), float(pos_weight), int(seed))
+    out = np.zeros(MLP_NPARAM, dtype=np.float32)
+    losses = np.zeros(int(epochs), dtype=np.float64)
+    init = None
+    if init_params is not None:
+        a, init = _fvec(init_params)
+    _check(load().hweno_indicator_train(C.c_void_p(_buf(feat)[0]), C.c_void_p(_buf(dev)[0]), n, C.byref(o), init,
+                                        out.ctypes.data_as(C.POINTER(C.c_float)),
+                                        losses.ctypes.data_as(C.POINTER(C.c_double)),
+                                        stream if stream is not None else _current_stream()))
+    return out, [float(x) for x in losses]
+
+
+def hweno_train_permutation(seed: int, epoch: int, n: int) -> np.ndarray:
+    out = np.empty(int(n), dtype=np.int32)
+    load().hweno_train_permutation(int(seed), int(epoch), int(n), out.ctypes.data_as(C.POINTER(C.c_int)))
+    return out
 
 
 def hweno_mlp_create(max_batch, stream=None):

@@ -84,27 +84,15 @@ def init_params(seed: int) -> np.ndarray:
 
 def train(data: Dataset, epochs: int = 6, batch: int = 4096, lr: float = 3e-3, seed: int = 0,
           delta: float = DELTA, pos_weight: float | None = None, verbose: bool = False):
-    """Adam on the GPU; returns (parameters, per-epoch mean losses)."""
-    import torch
-    y = (data.dev > delta).float()
-    pos = float(y.mean().item())
-    if pos_weight is None:
-        pos_weight = min(50.0, max(1.0, (1.0 - pos) / max(pos, 1e-6)))
-    m = hw.hweno_mlp_create(batch)
-    try:
-        hw.hweno_mlp_set_params(m, init_params(seed))
-        rng = np.random.default_rng(seed + 1)
-        losses = []
-        for ep in range(epochs):
-            perm = torch.from_numpy(rng.permutation(data.n).astype(np.int32)).cuda()
-            for b0 in range(0, data.n - batch + 1, batch):
-                hw.hweno_mlp_train_step(m, data.feat, data.dev, perm[b0:b0 + batch], delta, pos_weight, lr)
-            losses.append(hw.hweno_mlp_mean_loss(m))
-            if verbose:
-                print(f"epoch {ep}: loss {losses[-1]:.4f} (positives {pos:.3f}, pos_weight {pos_weight:.1f})")
-        theta = hw.hweno_mlp_get_params(m)
-    finally:
-        hw.hweno_mlp_destroy(m)
+    """Adam on the GPU through hweno_indicator_train (one C call: the epoch
+    loop, the seeded minibatch order and the class weight all live there);
+    returns (parameters, per-epoch mean losses)."""
+    theta, losses = hw.hweno_indicator_train(data.feat, data.dev, epochs, batch, lr, delta,
+                                             pos_weight=0.0 if pos_weight is None else pos_weight,
+                                             seed=seed, init_params=init_params(seed))
+    if verbose:
+        for ep, l in enumerate(losses):
+            print(f"epoch {ep}: loss {l:.4f}")
     return theta, losses
 
 

@@ -114,3 +114,29 @@ def test_batch_rejects_mixed_parameters():
     arr3 = (hw.hweno_config * 2)(c2.to_c(), c3.to_c())
     assert hw.load().hweno_batch_create(2, arr3, None, C.byref(h)) == hw.HWENO_ERR_ARG
     assert "batch-wide" in hw.hweno_last_error()
+
+
+def test_train_permutation_is_splitmix64_fisher_yates():
+    """The training order restated from the published definitions: SplitMix64
+    (Steele, Lea and Flood, 2014) from the state seed + (e + 1) *
+    0xD1B54A32D192ED03, Fisher-Yates from the top index down with
+    j = next() mod (i + 1).  Host code of the library; no GPU needed."""
+    M = (1 << 64) - 1
+
+    def perm(seed, e, n):
+        st = (seed + (e + 1) * 0xD1B54A32D192ED03) & M
+        out = list(range(n))
+        for i in range(n - 1, 0, -1):
+            st = (st + 0x9E3779B97F4A7C15) & M
+            z = st
+            z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+            z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+            z ^= z >> 31
+            j = z % (i + 1)
+            out[i], out[j] = out[j], out[i]
+        return out
+    from paper_2607_24325_b300 import hweno as hw
+    for seed, e, n in [(0, 0, 1), (0, 0, 17), (77, 3, 1000), (2 ** 63 + 5, 1, 333)]:
+        got = hw.hweno_train_permutation(seed, e, n)
+        assert got.tolist() == perm(seed, e, n)
+        assert sorted(got.tolist()) == list(range(n))
