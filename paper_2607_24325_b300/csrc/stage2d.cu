@@ -600,6 +600,34 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
 // (4% fewer FP64-pipe instructions in the mixed kernel than with the
 // run-time switches).  BATCH: the tiles of many 2D instances of uneven sizes
 // (a tile table; per-instance descriptors and control blocks).
+//
+// Tiles: with as many CTAs as tiles each CTA takes its own; a persistent
+// grid (fewer CTAs than tiles) starts every CTA on the tile of its index
+// and then hands out the rest in natural order from a global counter, so a
+// CTA whose tiles were cheap (no FP64 indicator work) takes more of them and
+// the SMs finish together.
+__device__ __forceinline__ int next_tile(unsigned* sched) {
+  __shared__ int s_next;
+  __syncthreads();  // every thread has read the previous s_next
+  if (threadIdx.x == 0) s_next = (int)(atomicAdd(&sched[0], 1u) + gridDim.x);
+  __syncthreads();
+  return s_next;
+}
+
+// After a CTA's last tile: the last CTA of the launch zeroes the scheduler
+// for the next launch (every other CTA has drawn its final tile by then).
+__device__ __forceinline__ void sched_finish(unsigned* sched) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned d = atomicAdd(&sched[1], 1u);
+    if (d == gridDim.x - 1) {
+      sched[0] = 0u;
+      sched[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
 template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
 __global__ void __launch_bounds__(threads2<T, W64>(), sizeof(T) == 4 ? 2 : 1) k_stage2d(const Stage2Args a) {
   constexpr int NC = EQ == HWENO_EQ_EULER ? 4 : 1;
@@ -655,10 +683,12 @@ __global__ void __launch_bounds__(threads2<T, W64>(), sizeof(T) == 4 ? 2 : 1) k_
     }
     const int tiles_x = (G.nx + kT2 - 1) / kT2;
     const int ntiles = tiles_x * ((G.ny + kT2 - 1) / kT2);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const bool dyn = a.sched != nullptr && (long long)gridDim.x < ntiles;
+    for (int tile = blockIdx.x; tile < ntiles; tile = dyn ? next_tile(a.sched) : tile + (int)gridDim.x) {
       const int i0 = (tile % tiles_x) * kT2, j0 = (tile / tiles_x) * kT2;
       tile2d<T, EQ, CHR, W64>(a, G, i0, j0, c, box, stash, wx, wx64, lin_all, g, advx_t, advy_t, radx, rady);
     }
+    if (dyn) sched_finish(a.sched);
     if (a.stage == 3) {
       radx = warp_max(radx);
       rady = warp_max(rady);
@@ -668,7 +698,8 @@ __global__ void __launch_bounds__(threads2<T, W64>(), sizeof(T) == 4 ? 2 : 1) k_
       }
     }
   } else {
-    for (long long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const bool dyn = a.sched != nullptr && (long long)gridDim.x < a.ntiles;
+    for (long long tile = blockIdx.x; tile < a.ntiles; tile = dyn ? next_tile(a.sched) : tile + gridDim.x) {
       const Tile2 tl = a.tiles[tile];
       const Inst2& I = a.inst[tl.inst];
       Ctl* ctl = a.ctl + tl.inst;
@@ -706,6 +737,7 @@ __global__ void __launch_bounds__(threads2<T, W64>(), sizeof(T) == 4 ? 2 : 1) k_
         rady = 0.0;
       }
     }
+    if (dyn) sched_finish(a.sched);
   }
 }
 
