@@ -870,3 +870,25 @@ def test_padded_state_2d_hand_written_ghosts():
     # y-moment of m_x in the right ghost column of row 0
     assert P[0, 2 + ny, 2 + nx] == U[0, ny - 1, nx - 1]  # rho: even under both mirrors
     assert P[9, 2, 2 + nx] == -U[9, 0, nx - 1]
+
+
+def test_alpha_and_dt_closed_form():
+    """Global Lax-Friedrichs constants (the largest |u| + c, |v| + c over the
+    cell averages) and the CFL step of Sec. 2.2, by hand: two cells with
+    (rho, u, v, p) = (1, 0.5, -2, 1) and (4, -1, 0.25, 2), gamma 1.4, so
+    c = sqrt(1.4) and sqrt(0.7); alpha_x = 1 + sqrt(0.7) (second cell),
+    alpha_y = 2 + sqrt(1.4) (first cell); dx = 1/2, dy = 1 on [0,1] x [0,1]
+    with 2 x 1 cells: dt = 0.6 / (alpha_x / 0.5 + alpha_y / 1)."""
+    prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=2, ny=1, lin_w=(0.99, 0.0025, 0.0025, 0.0025, 0.0025))
+    U = np.zeros((12, 1, 2))
+    for i, (r, u, v, p) in enumerate([(1.0, 0.5, -2.0, 1.0), (4.0, -1.0, 0.25, 2.0)]):
+        U[0:4, 0, i] = W.prim_to_cons_2d(r, u, v, p)
+    ax, ay = oracle.alpha(prob, U)
+    assert abs(ax - (1.0 + math.sqrt(0.7))) < 1e-15
+    assert abs(ay - (2.0 + math.sqrt(1.4))) < 1e-15
+    assert abs(oracle.dt(prob, ax, ay) - 0.6 / (ax / 0.5 + ay)) < 1e-17
+    p1 = oracle.Problem(dim=1, equation=oracle.EQ_BURGERS, nx=4, xhi=2.0)
+    ax1, _ = oracle.alpha(p1, np.array([[0.5, -3.0, 1.0, 2.0], [0.0] * 4]))
+    assert ax1 == 3.0 and oracle.dt(p1, ax1) == 0.6 * 0.5 / 3.0
+    p53 = oracle.Problem(dim=1, equation=oracle.EQ_ADVECTION, nx=8, xhi=1.0, dt_rule=oracle.DT_CFL_DX53)
+    assert abs(oracle.dt(p53, 1.0) - 0.6 * 0.125 ** (5.0 / 3.0)) < 1e-17
