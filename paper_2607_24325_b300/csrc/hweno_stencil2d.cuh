@@ -426,7 +426,7 @@ static __device__ __noinline__ Weights5 indicator64(const Stencil17 st, double e
 }
 
 // Mixed precision, Steps 2-3 for one field, FP32 part: the screen.  True
-// where every a_m = tau^2 / (beta_m^p + eps) is provably below 2^-28, so
+// where every a_m = tau^2 / (beta_m^p + eps) is provably below 2^-24, so
 // that 1 + a_m is 1 in FP32 and a_m = 0 gives the FP64 evaluation's result
 // bit for bit.
 __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
@@ -449,7 +449,7 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
   // and tau <= tau~ (1 + 2^-20) + D_0 + (D_1 + ... + D_4) / 4.  For the
   // moment form (weights w_l summing to 1331) Cauchy-Schwarz gives
   // G = 2 sum_l w_l |c~_l| <= 2 sqrt(1331 A) <= 72.97 sqrt(beta~_0), taken
-  // as 73 sqrt(beta~_0); likewise for the Jiang-Shu form with its matrix.  Where the bound puts every a_m below 2^-28 for
+  // as 73 sqrt(beta~_0); likewise for the Jiang-Shu form with its matrix.  Where the bound puts every a_m below 2^-25 for
   // all 32 lanes, 1 + a_m is 1 in FP32 whatever the FP64 evaluation gives,
   // so that evaluation is skipped and the result is the same bit for bit
   // (any sound bound keeps this; a looser one only skips less often).
@@ -499,7 +499,11 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
     for (int m = 1; m < 5; ++m) L = fminf(L, bs[m] - Ds[m]);
     L = fmaxf(L, 0.0f);
     const float dlo = (wf.pow2 ? L * L : L) + wf.eps;
-    quiet = ut2 < 0x1p-28f * dlo;
+    // ut, ut^2 and dlo carry at most a few FP32 roundings (relative 2^-21
+    // together), so ut2 < 2^-25 dlo puts the exact bound below 2^-24: the
+    // FP64 a_m, narrowed to FP32, is then at most 2^-24 and 1 + a_m rounds to
+    // 1 (to nearest, ties to even), as a_m = 0 gives
+    quiet = ut2 < 0x1p-25f * dlo;
   }
   return quiet;
 }
