@@ -76,7 +76,7 @@ MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.3  # executed, early-time 1536^2 state; dat
 # DRAM bytes per cell of the 2D Euler stage kernel, mean of the three stage
 # launches at 2048^2 (state larger than L2), scaled to the grid by cells;
 # None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 268.81, "fp32": 129.47, "fp32_ind64": 132.87}
+TRAFFIC_PER_CELL = {"fp64": 268.7, "fp32": 129.8, "fp32_ind64": 132.9}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 2048^2, scaled to the grid by cells"
 # Stored fields F and limited-derivative fields D per cell: stage 1 reads F
 # and writes F + D, stages 2-3 read 2F and write F -> (8F + D)/3 words per
@@ -566,7 +566,7 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
             if r["learned"]:
                 roof["note"] = ("effective: the plain scheme's algorithmic count; the linear path skips Steps 2-3 "
                                 "and the projections on the cells the network clears")
-            if r["precision"] == hw.FP32_IND64 and key == "euler2d_char":
+            if r["precision"] == hw.FP32_IND64 and key == "euler2d_char" and workload == "euler2d_quadrant":
                 roof["fp64_flops_per_cell_stage"] = MIXED_FP64_FLOPS_PER_CELL_STAGE
                 roof["fp64_frac"] = (MIXED_FP64_FLOPS_PER_CELL_STAGE * cells_rank / (r["stage_ms"] * 1e-3) / 1e12
                                      / alu_peak_tflops("f64", dev["sms"], dev["mhz"]))
