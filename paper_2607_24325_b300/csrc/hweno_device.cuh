@@ -61,6 +61,7 @@ struct WeightsT {
   int pow2;      // 1: beta^2 + eps in the denominator, 0: beta + eps
   int linear;    // 1: omega = gamma (pure p0)
   int typical;   // 1: Jiang-Shu integral indicator for p0
+  int screen_off;  // 1: the FP32 screens clear nothing (verification)
 };
 
 template <typename T>
@@ -78,6 +79,7 @@ __host__ __device__ inline WeightsT<T> make_weights(const WeightParams& w) {
   o.pow2 = w.pow2;
   o.linear = w.linear;
   o.typical = w.typical;
+  o.screen_off = w.screen_off;
   return o;
 }
 
@@ -240,6 +242,42 @@ __device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<
 template <typename T>
 struct Rec1 { T uL, uR, dL, dR, vh; };
 
+// Mixed precision, 1D, the FP32 screen: true where every a_m = tau^2 /
+// (beta_m^p + eps) of Step 3 is provably at most 2^-24.  The argument of the
+// 2D screen on the 1D maps: the coefficients from centre-shifted FP32
+// differences (dm = u_{i-1} - u_i, dp = u_{i+1} - u_i, a = dx v_{i-1},
+// b = dx v_{i+1}; every map constant exact in binary) err by a few u S at
+// most (S the largest of |dm|, |dp|, |a|, |b|, u = 2^-24), bounded here by
+// E = 2^-16 S; beta_0 = sum_l w_l c_l^2 (w = 1, 4, 36, 576, sum 617) then errs
+// by at most 2^-18 beta~_0 + E (2 sum_l w_l |c~_l| + 617 E), and
+// 2 sum_l w_l |c~_l| <= 2 sqrt(617 beta~_0) <= 50 sqrt(beta~_0) (Cauchy-Schwarz);
+// beta_1 = dm^2 and beta_2 = dp^2 err by 2^-20 of themselves.  tau is at
+// most tau~ (1 + 2^-20) + D_0 + (D_1 + D_2)/2, every beta_m at least its
+// value less its bound, and ut^2 < 2^-25 dlo leaves room for the screen's
+// own rounding below 2^-24.  The Jiang-Shu form always takes the FP64 path.
+__device__ __forceinline__ bool screen1(float um, float u0, float up, float a, float b, const WeightsT<float>& wf) {
+  // the verification build (libhweno_noscreen.so) sets screen_off on the host:
+  // every lane then takes the FP64 indicator
+  if (wf.typical || wf.screen_off) return false;
+  const float dm = um - u0, dp = up - u0;
+  const float S = fmaxf(fmaxf(fabsf(dm), fabsf(dp)), fmaxf(fabsf(a), fabsf(b)));
+  const float E = S * 0x1p-16f;
+  const float sd = dm + dp, df = dp - dm, ab = a + b, ba = b - a;
+  const float c1 = 0.8125f * df - 0.3125f * ab;
+  const float c2 = 1.25f * sd - 0.375f * ba;
+  const float c3 = 0.25f * (ab - df);
+  const float c4 = 0.25f * ba - 0.5f * sd;
+  const float b0 = c1 * c1 + 4.0f * (c2 * c2) + 36.0f * (c3 * c3) + 576.0f * (c4 * c4);
+  const float b1 = dm * dm, b2 = dp * dp;
+  const float D0 = 0x1p-18f * b0 + E * (50.0f * sqrt_approx(b0) + 617.0f * E);
+  const float D1 = 0x1p-20f * b1, D2 = 0x1p-20f * b2;
+  const float tau = 0.5f * (fabsf(b0 - b1) + fabsf(b0 - b2));
+  const float ut = tau * (1.0f + 0x1p-20f) + D0 + 0.5f * (D1 + D2);
+  const float L = fmaxf(fminf(fminf(b0 - D0, b1 - D1), b2 - D2), 0.0f);
+  const float dlo = (wf.pow2 ? L * L : L) + wf.eps;
+  return ut * ut < 0x1p-25f * dlo;
+}
+
 template <typename T, bool W64 = false>
 __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T idx,
                                           const WeightsT<T>& w, const WeightsT<double>* w64 = nullptr) {
@@ -257,22 +295,38 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
   if (w.linear) {
     r = T(1); w1 = w.g[1]; w2 = w.g[2];
   } else if constexpr (W64) {
-    // mixed precision: the indicator coefficients, indicators and weights in FP64
-    const double Um = to_tc<double>(um), U0 = to_tc<double>(u0), Up = to_tc<double>(up), Dx = to_tc<double>(dx);
-    const double A = Dx * to_tc<double>(vm), Bv = Dx * to_tc<double>(vp);
-    const double S = Um + Up, D = Up - Um, AB = A + Bv, BA = Bv - A;
-    const double e1 = 13.0 / 16.0 * D - 5.0 / 16.0 * AB;
-    const double e2 = 5.0 / 4.0 * S - 5.0 / 2.0 * U0 - 3.0 / 8.0 * BA;
-    const double e3 = 0.25 * (AB - D);
-    const double e4 = U0 - 0.5 * S + 0.25 * BA;
-    const double f1 = U0 - Um, f2 = Up - U0;
-    double beta[3] = {w.typical ? beta_typical_1d(e1, e2, e3, e4)
-                                : e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4,
-                      f1 * f1, f2 * f2};
-    const double tau = 0.5 * (fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
-    double r64, om[3];
-    nl_weights<double, 2>(beta, tau, *w64, r64, om);
-    r = narrow_f64(r64); w1 = narrow_f64(om[1]); w2 = narrow_f64(om[2]);
+    // mixed precision (the same rule as in 2D): a_m = tau^2 / (beta_m^p + eps)
+    // from FP64 indicators, rounded to FP32, wherever the FP32 screen cannot
+    // show that every a_m is at most 2^-24 for the whole warp (then 1 + a_m
+    // rounds to 1 in FP32 and a_m = 0 gives the same weights bit for bit);
+    // the weights w~_m = gamma_m (1 + a_m) and their normalisation in FP32.
+    float am[3] = {0.0f, 0.0f, 0.0f};
+    if (!__all_sync(HW_FULL_MASK, screen1(um, u0, up, a, b, w))) {
+      const double Um = to_tc<double>(um), U0 = to_tc<double>(u0), Up = to_tc<double>(up), Dx = to_tc<double>(dx);
+      const double A = Dx * to_tc<double>(vm), Bv = Dx * to_tc<double>(vp);  // exact products
+      const double S = Um + Up, D = Up - Um, AB = A + Bv, BA = Bv - A;
+      const double e1 = 13.0 / 16.0 * D - 5.0 / 16.0 * AB;
+      const double e2 = 5.0 / 4.0 * S - 5.0 / 2.0 * U0 - 3.0 / 8.0 * BA;
+      const double e3 = 0.25 * (AB - D);
+      const double e4 = U0 - 0.5 * S + 0.25 * BA;
+      const double f1 = U0 - Um, f2 = Up - U0;
+      const double beta[3] = {w.typical ? beta_typical_1d(e1, e2, e3, e4)
+                                        : e1 * e1 + 4.0 * e2 * e2 + 36.0 * e3 * e3 + 576.0 * e4 * e4,
+                              f1 * f1, f2 * f2};
+      const double tau = 0.5 * (fabs(beta[0] - beta[1]) + fabs(beta[0] - beta[2]));
+      const double t2 = tau * tau;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double d = (w64->pow2 ? beta[m] * beta[m] : beta[m]) + w64->eps;
+        am[m] = narrow_f64_ftz(t2 * rcp_newton(d));
+      }
+    }
+    const float e0 = opaque(w.g[0] * (1.0f + am[0])), ew1 = opaque(w.g[1] * (1.0f + am[1]));
+    const float ew2 = opaque(w.g[2] * (1.0f + am[2]));
+    const float inv = rcp_approx((e0 + ew1) + ew2);
+    r = opaque((1.0f + am[0]) * inv);
+    w1 = opaque(ew1 * inv);
+    w2 = opaque(ew2 * inv);
   } else {
     // Step 2: beta = sum_l (l! c_l)^2
     T beta[3];

@@ -431,11 +431,10 @@ static __device__ __noinline__ Weights5 indicator64(const Stencil17 st, double e
 // bit for bit.
 __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
                                         const WeightsT<float>& wf) {
-#ifdef HWENO_SCREEN_OFF
-  // verification build (libhweno_noscreen.so): every lane takes the FP64
+  // verification build (libhweno_noscreen.so, which sets screen_off on the
+  // host and compiles the same device code): every lane takes the FP64
   // indicator, to show that the screen never changes an output bit
-  return false;
-#endif
+  if (wf.screen_off) return false;
   const float q5f = q[4];
   // FP32 screen: a sound upper bound on every a_m = tau^2 / (beta_m^p + eps)
   // from the FP32 coefficients k.  Each c~_l combines the stencil differences

@@ -15,6 +15,10 @@ struct WeightParams {
   int pow2;
   int linear;
   int typical;   // 1: Jiang-Shu integral indicator for p0
+  // 1: the mixed precision's FP32 screens clear nothing (every lane takes
+  // the FP64 indicator).  Set on the host only, by the screen-off
+  // verification build, so that both builds compile the same device code.
+  int screen_off;
   // the same in FP32, rounded on the host: FP32 kernels read these
   // parameters directly (a conversion re-done at every use would issue on
   // the FP64 pipe)
@@ -36,6 +40,11 @@ inline WeightParams weight_params(const hweno_config& c) {
   w.pow2 = c.weight_pow == 2;
   w.linear = c.linear_weights != 0;
   w.typical = c.smoothness == HWENO_BETA_TYPICAL;
+#ifdef HWENO_SCREEN_OFF
+  w.screen_off = 1;
+#else
+  w.screen_off = 0;
+#endif
   return w;
 }
 
