@@ -4,7 +4,7 @@ rounds to 1 in FP32).  So the library and a build with the screen off
 (libhweno_noscreen.so: every lane of every row takes the FP64 indicator)
 must give the same output bits: operator application and eight steps on
 five kinds of 2D state and three of 1D, with both smoothness-indicator
-forms.  The library is
+forms, and a batch of three 2D problems (the batched kernel).  The library is
 chosen at load time, so each build runs in a child process."""
 import os
 import subprocess
@@ -63,6 +63,20 @@ for name, cfg, U in cases:
         h.update(np.ascontiguousarray(a).tobytes())
     print("HASH", name, h.hexdigest())
     s.close()
+# the batched 2D kernel: three four-quadrant problems of uneven sizes in one launch per stage
+sizes = [(96, 70), (61, 128), (150, 33)]
+cfgs = [hw.Config(dim=2, nx=nx, ny=ny, equation=hw.EQ_EULER, lin_w=W2D, bc=(1,) * 4, precision=hw.FP32_IND64)
+        for nx, ny in sizes]
+b = hw.Batch(cfgs)
+b.set_state(b.pack([W.quadrant_2d(W.quadrant_states(40 + k), 0.45, 0.55, 0, 1, 0, 1, nx, ny)
+                    for k, (nx, ny) in enumerate(sizes)]))
+L, D = b.apply_operator([(3.0, 2.5)] * 3)
+b.advance(1e30, max_steps=8)
+h = hashlib.sha256()
+for a in (L.cpu().numpy(), D.cpu().numpy(), b.get_state(device=False)):
+    h.update(np.ascontiguousarray(a).tobytes())
+print("HASH", "batch2d", h.hexdigest())
+b.close()
 '''
 
 
@@ -79,4 +93,4 @@ def test_screen_changes_no_output_bit():
     __graft_entry__.build()
     screened = _hashes({})
     full = _hashes({"HWENO_NOSCREEN": "1"})
-    assert len(screened) == 16 and screened == full, (screened, full)
+    assert len(screened) == 17 and screened == full, (screened, full)
