@@ -678,9 +678,10 @@ def run_single_grid(args, hw, torch, world, rank, local, workload, cfg_kw, U0, a
         s.set_state(U0.cuda())
         ms, stage_ms, _, launches, clk = time_steps(s, torch, args.steps, flush=flush, clock_gpu=local)
         s.close()
+        ms = max_over_ranks(ms)   # under torchrun every rank advances its own copy (replicas)
         kind = "f64" if prec == hw.FP64 else "f32"
         pname = {hw.FP64: "FP64", hw.FP32: "FP32", hw.FP32_IND64: "FP32_IND64"}[prec]
-        out[name] = {"value": cells * 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+        out[name] = {"value": world * cells * 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
                      "dtype": DTYPE[pname],
                      "roofline": roofline(algo_key, cells, stage_ms, kind, dev["sms"], dev["mhz"], pname),
                      "hbm": hbm_fraction(fkind, 8 if kind == "f64" else 4, cells, stage_ms, dev["hbm"],
@@ -690,13 +691,14 @@ def run_single_grid(args, hw, torch, world, rank, local, workload, cfg_kw, U0, a
     head = "fp64"
     if rank == 0:
         h = out[head]
-        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        line = {"metric": METRIC, "value": h["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": h["dtype"],
                 "data": "synthetic (closed-form initial data)",
-                "config": {"workload": workload + ", arm fp64", "cells": cells,
+                "config": {"workload": workload + ", arm fp64", "cells": cells * world,
                            "l2": "flushed (256 MB write) before every timed step" if flush_l2
-                           else "inputs larger than L2"},
+                           else "inputs larger than L2",
+                           "parallelism": "single GPU" if world == 1 else f"replicas on {world} GPUs"},
                 "roofline": h["roofline"], "hbm": h["hbm"], "gpu_launches": h["gpu_launches"],
                 "clocks": merge_clocks(clocks), "arms": out}
         print(json.dumps(line), flush=True)
