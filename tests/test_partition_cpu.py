@@ -247,3 +247,43 @@ def test_a_missing_exchange_is_detected():
     diff = max(np.abs(e.buf[0][:, s.halo_lo:s.halo_lo + s.own, :] - ref[:, s.rows[0]:s.rows[1], :]).max()
                for s, e in zip(slabs, execs))
     assert diff > 1e-8
+
+
+def test_bench_slabs_of_stacked_copies_equal_the_stacked_grid():
+    """The bench's weak-scaling layout: `world` copies of one state stacked
+    along y, one copy's rows per rank (BenchSlab).  Each rank's local state
+    and config come from the copy alone; advanced with the oracle as the
+    executor, the slabs equal the explicitly stacked grid run as one."""
+    from dataclasses import dataclass
+
+    @dataclass
+    class Cfg:                     # the fields of hw.Config the slab set-up reads
+        nx: int
+        ny: int
+        xlo: float = 0.0
+        xhi: float = 1.5
+        ylo: float = 0.0
+        yhi: float = 1.0
+        cfl: float = 0.6
+        dt_rule: int = 0
+        bc: tuple = (oracle.BC_PERIODIC, oracle.BC_PERIODIC, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW)
+    world, nx, ny = 3, 12, 8
+    cfg = Cfg(nx=nx, ny=ny, yhi=ny / 8.0)
+    prob1 = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=nx, ny=ny, xhi=1.5, yhi=ny / 8.0, lin_w=W2D,
+                           bc=cfg.bc)
+    U = _initial(prob1)
+    stacked = oracle.Problem(**{**prob1.__dict__, "ny": ny * world, "yhi": ny * world / 8.0})
+    ref = _reference(stacked, np.concatenate([U] * world, axis=1), 2)
+    slabs, execs = [], []
+    for r in range(world):
+        bs = PT.BenchSlab.for_rank(cfg, U, world, r)
+        assert bs.cfg_global.ny == ny * world and bs.slab.own == ny
+        lc = bs.slab.local_config(bs.cfg_global)
+        lp = oracle.Problem(**{**prob1.__dict__, "ny": lc.ny, "ylo": lc.ylo, "yhi": lc.yhi, "bc": tuple(lc.bc)})
+        slabs.append(bs.slab)
+        execs.append(OracleSlab(lp, bs.local_state()))
+    grp = PT.SlabGroup(PT.BenchSlab.for_rank(cfg, U, world, 0).cfg_global, slabs, execs, PT.LocalComm())
+    grp.step()
+    grp.step()
+    for s, e in zip(slabs, execs):
+        assert np.array_equal(e.buf[0][:, s.halo_lo:s.halo_lo + s.own, :], ref[:, s.rows[0]:s.rows[1], :]), s.rank
