@@ -27,6 +27,7 @@ ranks bracket the timed region.
 from __future__ import annotations
 
 import argparse
+import functools
 import json
 import os
 import statistics
@@ -184,7 +185,10 @@ def merge_clocks(parts) -> dict:
 
 
 # ----------------------------------------------------------------- workloads
+@functools.lru_cache(maxsize=2)
 def quadrant_state(n: int) -> np.ndarray:
+    """The four-quadrant initial state (built once per grid size; callers
+    only read it)."""
     from paper_2607_24325_b300 import workloads as W
     return W.quadrant_2d(W.quadrant_states(SEED), 0.5, 0.5, 0.0, 1.0, 0.0, 1.0, n, n)
 
@@ -434,45 +438,105 @@ def oracle_comparison(hw, torch, make_problem, plan, theta, T):
     return out
 
 
-def run_euler2d(args, hw, torch, world, rank, local, workload):
-    """A single 2D Euler grid (the four-quadrant headline or the shock /
-    entropy-wave family), every arm timed on the same state; the FP64 arm is
-    the headline."""
+def problem_factory(hw, workload, ng):
+    """(make_problem(n, precision, options) -> (config, initial state, oracle
+    problem), the oracle-comparison time, the data note, the workload name)
+    of a single 2D Euler workload."""
     from paper_2607_24325_b300 import indicator as IND
     from paper_2607_24325_b300 import workloads as W
     import oracle
-    torch.cuda.set_device(local)
-    dev = device_facts(torch, local)
-    ng = args.grid if workload == "euler2d_quadrant" else args.grid_se
-
     if workload == "euler2d_quadrant":
         def make_problem(n, prec=hw.FP64, extra=None):
             U = quadrant_state(n)
             prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=n, ny=n, lin_w=W2D,
                                   bc=(oracle.BC_OUTFLOW,) * 4, **_oracle_opts(extra))
             return euler_cfg(hw, n, prec, extra), U, prob
-        T_cmp = 0.002
-        data = "synthetic (seeded four-quadrant Riemann states, seed 2024)"
-        wname = (f"2D Euler four-quadrant Riemann {ng}^2, transmissive, characteristic-wise nonlinear HWENO, "
-                 f"SSP-RK3")
-    else:
-        se_seed = 11
+        return (make_problem, 0.002, "synthetic (seeded four-quadrant Riemann states, seed 2024)",
+                f"2D Euler four-quadrant Riemann {ng}^2, transmissive, characteristic-wise nonlinear HWENO, SSP-RK3")
+    se_seed = 11
+    states = {}   # the initial state per grid size (it does not depend on the arm)
 
-        def make_problem(n, prec=hw.FP64, extra=None):
-            cfg, U = IND.shock_entropy_problem(se_seed, n, prec)
-            for k, v in (extra or {}).items():
-                setattr(cfg, k, v)
-            prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=n, ny=n, lin_w=W2D,
-                                  bc=(oracle.BC_INFLOW, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW),
-                                  bc_state=[list(cfg.bc_state[0]), [0.0] * 4, [0.0] * 4, [0.0] * 4],
-                                  **_oracle_opts(extra))
-            return cfg, U, prob
-        T_cmp = 0.004
+    def make_problem(n, prec=hw.FP64, extra=None):
+        if n not in states:
+            states[n] = IND.shock_entropy_problem(se_seed, n, hw.FP64)[1]
+        U = states[n]
+        cfg = IND.shock_entropy_config(n, prec)   # inflow of the post-shock state on the left
         prm = W.shock_entropy_2d(seed=se_seed).params
-        data = f"synthetic (shock / entropy-wave family, seed {se_seed})"
-        wname = (f"2D Euler shock / entropy wave {ng}^2 (Mach {prm['mach']:.2f} shock into rho = 1 + 0.2 "
-                 f"sin(k x.n), k = {prm['k'] / np.pi:.0f} pi), inflow + transmissive, characteristic-wise "
-                 f"nonlinear HWENO, SSP-RK3")
+        cfg.bc_state = [list(W.prim_to_cons_2d(prm["rho2"], prm["u2"], 0.0, prm["p2"])), [0.0] * 4, [0.0] * 4,
+                        [0.0] * 4]
+        for k, v in (extra or {}).items():
+            setattr(cfg, k, v)
+        prob = oracle.Problem(dim=2, equation=oracle.EQ_EULER, nx=n, ny=n, lin_w=W2D,
+                              bc=(oracle.BC_INFLOW, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW, oracle.BC_OUTFLOW),
+                              bc_state=[list(cfg.bc_state[0]), [0.0] * 4, [0.0] * 4, [0.0] * 4],
+                              **_oracle_opts(extra))
+        return cfg, U, prob
+    prm = W.shock_entropy_2d(seed=se_seed).params
+    return (make_problem, 0.004, f"synthetic (shock / entropy-wave family, seed {se_seed})",
+            f"2D Euler shock / entropy wave {ng}^2 (Mach {prm['mach']:.2f} shock into rho = 1 + 0.2 "
+            f"sin(k x.n), k = {prm['k'] / np.pi:.0f} pi), inflow + transmissive, characteristic-wise "
+            f"nonlinear HWENO, SSP-RK3")
+
+
+def time_solver_arm(hw, torch, cfg, U0, steps, warmup, local, theta=None):
+    """One arm on one GPU: autotune, warm-up, then `steps` profiled steps
+    from the initial state."""
+    s = hw.Solver(cfg)
+    if theta is not None:
+        hw.hweno_indicator_load(s.h, theta, 0.5)
+    U0_dev = torch.from_numpy(U0).cuda()
+    s.set_state(U0_dev)
+    hw.hweno_autotune(s.h, reps=2)
+    s.advance(1e30, max_steps=warmup)
+    s.set_state(U0_dev)   # the timed steps start from the workload's initial state
+    ms, stage_ms, stage_n, launches, clk = time_steps(s, torch, steps, clock_gpu=local)
+    rho = s.get_state()[0].double().clone()
+    smooth = None
+    if theta is not None:
+        sm = torch.empty((cfg.nx * cfg.ny,), dtype=torch.uint8, device="cuda")
+        hw.hweno_indicator_mask(s.h, sm, None)
+        smooth = float(sm.float().mean().item())
+    s.close()
+    return {"ms": ms, "stage_ms": stage_ms, "stage_launches": stage_n, "launches": launches, "clocks": clk,
+            "rho": rho, "smooth_fraction": smooth}
+
+
+def config5_learned(args, hw, torch, local, theta):
+    """The learned indicator where it was built for (the shock / entropy-wave
+    family, 2048^2): the plain FP64 path, the plain mixed path and the mixed
+    path with the learned indicator, each timed on the GPU and compared with
+    the oracle on the 256^2 problem (matched L1)."""
+    ng = args.grid_se
+    make_problem, T_cmp, _, wname = problem_factory(hw, "shock_entropy", ng)
+    plan = [("fp64", hw.FP64, False, {}), ("fp32_ind64", hw.FP32_IND64, False, {}),
+            ("fp32_ind64_learned", hw.FP32_IND64, True, {})]
+    steps = min(args.steps, 5)
+    out = {}
+    for name, prec, learned, extra in plan:
+        cfg, U0, _ = make_problem(ng, prec, extra)
+        r = time_solver_arm(hw, torch, cfg, U0, steps, min(args.warmup, 3), local, theta if learned else None)
+        out[name] = {"value": ng * ng * 3 * steps / (r["ms"] * 1e-3), "ms_per_step": r["ms"] / steps}
+        if r["smooth_fraction"] is not None:
+            out[name]["linear_path_fraction"] = r["smooth_fraction"]
+    cmp = oracle_comparison(hw, torch, make_problem, plan, theta, T_cmp)
+    for name in out:
+        out[name]["rel_l1_rho_vs_oracle_256"] = cmp[name]
+    le, pm, pf = out["fp32_ind64_learned"], out["fp32_ind64"], out["fp64"]
+    return {"workload": wname, "steps": steps, "arms": out,
+            "learned_speedup_vs_fp64": le["value"] / pf["value"],
+            "learned_speedup_vs_plain_mixed": le["value"] / pm["value"],
+            "l1_learned_over_plain_mixed": le["rel_l1_rho_vs_oracle_256"] / pm["rel_l1_rho_vs_oracle_256"],
+            "oracle_grid": "256^2", "oracle_t_final": T_cmp}
+
+
+def run_euler2d(args, hw, torch, world, rank, local, workload):
+    """A single 2D Euler grid (the four-quadrant headline or the shock /
+    entropy-wave family), every arm timed on the same state; the FP64 arm is
+    the headline."""
+    torch.cuda.set_device(local)
+    dev = device_facts(torch, local)
+    ng = args.grid if workload == "euler2d_quadrant" else args.grid_se
+    make_problem, T_cmp, data, wname = problem_factory(hw, workload, ng)
 
     plan = [(name, getattr(hw, prec), learned,
              {k: getattr(hw, v) if isinstance(v, str) else v for k, v in extra.items()})
@@ -500,25 +564,7 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
             r = PT.time_slab_arm(hw, torch, PT.BenchSlab.for_rank(cfg, U0, world, rank), args.steps, args.warmup,
                                  local, theta if learned else None)
         else:
-            s = hw.Solver(cfg)
-            if learned:
-                hw.hweno_indicator_load(s.h, theta, 0.5)
-            U0_dev = torch.from_numpy(U0).cuda()
-            s.set_state(U0_dev)
-            hw.hweno_autotune(s.h, reps=2)
-            s.advance(1e30, max_steps=args.warmup)
-            s.set_state(U0_dev)   # the timed steps start from the workload's initial state
-            ms, stage_ms, stage_n, launches, clk = time_steps(s, torch, args.steps, clock_gpu=local)
-            rho = s.get_state()[0].double().clone()
-            smooth = None
-            if learned:
-                sm = torch.empty((ng * ng,), dtype=torch.uint8, device="cuda")
-                hw.hweno_indicator_mask(s.h, sm, None)
-                smooth = float(sm.float().mean().item())
-            s.close()
-            del U0_dev
-            r = {"ms": ms, "stage_ms": stage_ms, "stage_launches": stage_n, "launches": launches, "clocks": clk,
-                 "rho": rho, "smooth_fraction": smooth}
+            r = time_solver_arm(hw, torch, cfg, U0, args.steps, args.warmup, local, theta if learned else None)
         r.update({"precision": prec, "learned": learned, "extra": extra})
         arms[name] = r
     for name in arms:   # every rank, same order: each arm's time is its slowest rank's
@@ -534,6 +580,10 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
         cfg, U0, _ = make_problem(ng, arms[head_name]["precision"])
         e2e = PT.e2e_slab(hw, torch, PT.BenchSlab.for_rank(cfg, U0, world, rank), args.steps)
         e2e["value"] = world * e2e.pop("units") / max_over_ranks(e2e.pop("seconds"))
+
+    c5 = None
+    if workload == "euler2d_quadrant" and world == 1 and args.only is None and not args.no_config5:
+        c5 = config5_learned(args, hw, torch, local, theta)
 
     cmp = None
     cpu = None
@@ -606,6 +656,8 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
             "oracle_comparison": cmp,
             "learned_indicator": ind_eval,
         }
+        if c5 is not None:
+            line["config5_learned"] = c5
         if "fp32_ind64_learned" in summ and "fp64" in summ:
             la, pa = summ["fp32_ind64_learned"], summ["fp64"]
             line["learned_vs_plain_fp64"] = {
@@ -811,6 +863,8 @@ def main():
     ap.add_argument("--only", choices=[a[0] for a in ARMS], default=None,
                     help="time one arm only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the shock / entropy-wave section of the default line")
     ap.add_argument("--workload", choices=["euler2d_quadrant", "shock_entropy", "batch1d", "batch2d", "dmr",
                                            "advection1d", "burgers2d"],
                     default="euler2d_quadrant",
