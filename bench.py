@@ -9,7 +9,10 @@ kernels plus the device-resident time-step control); the metric is
 cell-updates per RK stage per second.  The FP32 and mixed-precision arms, the
 learned-indicator arms and two scheme variants are timed on the same state
 and reported under "arms", each with its relative L1 error against the FP64
-path and against the CPU oracle on the 256^2 version of the problem.
+path and against the CPU oracle on the 256^2 version of the problem.  The
+default line also carries "config5_learned": the shock / entropy-wave family
+at 2048^2 with the plain FP64, plain mixed and learned mixed paths timed and
+compared with the oracle (the learned indicator's gain at matched L1).
 
 Every workload line (--workload) carries a roofline: the algorithmic flops of
 a cell update in one stage (the method's formulas in plain evaluation, the
