@@ -10,7 +10,7 @@ cell-updates per RK stage per second.  The FP32 and mixed-precision arms, the
 learned-indicator arms and two scheme variants are timed on the same state
 and reported under "arms", each with its relative L1 error against the FP64
 path and against the CPU oracle on the 256^2 version of the problem.  The
-default line also carries "config5_learned": the shock / entropy-wave family
+default line also carries "shock_entropy_learned": the shock / entropy-wave family
 at 2048^2 with the plain FP64, plain mixed and learned mixed paths timed and
 compared with the oracle (the learned indicator's gain at matched L1).
 
@@ -504,7 +504,7 @@ def time_solver_arm(hw, torch, cfg, U0, steps, warmup, local, theta=None):
             "rho": rho, "smooth_fraction": smooth}
 
 
-def config5_learned(args, hw, torch, local, theta):
+def shock_entropy_learned(args, hw, torch, local, theta):
     """The learned indicator where it was built for (the shock / entropy-wave
     family, 2048^2): the plain FP64 path, the plain mixed path and the mixed
     path with the learned indicator, each timed on the GPU and compared with
@@ -584,9 +584,9 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
         e2e = PT.e2e_slab(hw, torch, PT.BenchSlab.for_rank(cfg, U0, world, rank), args.steps)
         e2e["value"] = world * e2e.pop("units") / max_over_ranks(e2e.pop("seconds"))
 
-    c5 = None
-    if workload == "euler2d_quadrant" and world == 1 and args.only is None and not args.no_config5:
-        c5 = config5_learned(args, hw, torch, local, theta)
+    se = None
+    if workload == "euler2d_quadrant" and world == 1 and args.only is None and not args.no_shock_entropy:
+        se = shock_entropy_learned(args, hw, torch, local, theta)
 
     cmp = None
     cpu = None
@@ -659,8 +659,8 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
             "oracle_comparison": cmp,
             "learned_indicator": ind_eval,
         }
-        if c5 is not None:
-            line["config5_learned"] = c5
+        if se is not None:
+            line["shock_entropy_learned"] = se
         if "fp32_ind64_learned" in summ and "fp64" in summ:
             la, pa = summ["fp32_ind64_learned"], summ["fp64"]
             line["learned_vs_plain_fp64"] = {
@@ -866,7 +866,7 @@ def main():
     ap.add_argument("--only", choices=[a[0] for a in ARMS], default=None,
                     help="time one arm only (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-config5", action="store_true",
+    ap.add_argument("--no-shock-entropy", action="store_true",
                     help="skip the shock / entropy-wave section of the default line")
     ap.add_argument("--workload", choices=["euler2d_quadrant", "shock_entropy", "batch1d", "batch2d", "dmr",
                                            "advection1d", "burgers2d"],

@@ -5,7 +5,7 @@ What pins what:
     from the constraint definitions of Step 1 (Sec. 2.1, 2.2).
   * exact polynomial reproduction (degree <= 4, any positive linear weights;
     degree <= 1 with nonlinear weights)          <- closed form.
-  * the paper's accuracy tables (Sec. 4.1, HWENO rows) and fifth-order rates
+  * the paper's accuracy tables (Sec. 3.1, HWENO rows) and fifth-order rates
     against exact solutions                      <- printed values / exact PDE solutions.
   * conservation (periodic and reflective walls), x<->y symmetry, Euler
     Jacobian = derivative of the flux, A R = R Lambda, L R = I.
