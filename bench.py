@@ -100,6 +100,18 @@ ARMS = [("fp64", "FP64", False, {}), ("fp32", "FP32", False, {}), ("fp32_ind64",
 DTYPE = {"FP64": "f64", "FP32": "f32", "FP32_IND64": "f32 (f64 indicators/weights)"}
 
 
+def host_cpu() -> str:
+    """Model name of the host CPU the oracle runs on (from /proc/cpuinfo)."""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def words_per_cell_stage(kind: str) -> float:
     F, D = FIELDS[kind]
     return (8 * F + D) / 3.0
@@ -219,7 +231,7 @@ def cpu_oracle_rate(m: int, steps: int = 1) -> dict:
     for _ in range(steps):
         U = oracle.step(prob, U, dt, ax, ay)
     el = time.perf_counter() - t0
-    return {"value": m * m * 3 * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": m * m * 3 * steps / el, "unit": UNIT, "cores": 1, "cpu": host_cpu(), "kind": "oracle",
             "sample": f"{steps} SSP-RK3 step(s) of the serial FP64 C oracle on a {m}x{m} window of the "
                       f"4096^2 four-quadrant state ({el:.1f} s)"}
 
@@ -296,7 +308,7 @@ def run_reference(args, world, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded four-quadrant Riemann states)",
         "config": headline_config(args.grid, 1, "fp64"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "cpu": host_cpu(), "kind": "oracle",
                          "sample": f"one SSP-RK3 step of the serial C oracle on a {m}x{m} window per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -595,7 +607,7 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
         if workload == "euler2d_quadrant":
             cpu = cpu_oracle_rate(256, steps=2)
         else:
-            cpu = {"value": 256 * 256 * 3 * cmp["oracle_steps"] / cmp["oracle_seconds"], "unit": UNIT, "cores": 1,
+            cpu = {"value": 256 * 256 * 3 * cmp["oracle_steps"] / cmp["oracle_seconds"], "unit": UNIT, "cores": 1, "cpu": host_cpu(),
                    "kind": "oracle", "sample": f"{cmp['oracle_steps']} SSP-RK3 steps of the serial FP64 C oracle on "
                                                f"the 256^2 version of the workload ({cmp['oracle_seconds']:.1f} s)"}
 
@@ -857,7 +869,7 @@ def run_dmr(args, hw, torch, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
