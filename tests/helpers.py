@@ -78,3 +78,26 @@ def within_spread(got, ref, spread, floor, factor=100.0):
     e = plane_errs(got, ref)
     tol = np.maximum(floor, factor * np.asarray(spread))
     return bool(np.all(e <= tol)), e, tol
+
+
+def window_operator(prob, U, i, j, ax, ay, r=3, rel=0.0, samples=4):
+    """Oracle L and D at cell (i, j) from a (2r+1)^2 window around it (the
+    operator at a cell depends on a radius-2 neighbourhood only), and their
+    absolute spread under random relative input perturbations of size `rel`
+    (the condition of that cell's outputs at the working precision)."""
+    sub = np.ascontiguousarray(U[:, j - r:j + r + 1, i - r:i + r + 1])
+    m = 2 * r + 1
+    p = oracle.Problem(dim=2, equation=prob.equation, nx=m, ny=m, xlo=0, xhi=m * prob.dx, ylo=0,
+                       yhi=m * prob.dy, lin_w=prob.lin_w, eps=prob.eps, weight_pow=prob.weight_pow,
+                       charwise=prob.charwise, gamma_gas=prob.gamma_gas, smoothness=prob.smoothness,
+                       bc=(1, 1, 1, 1))
+    L, D = oracle.operator(p, sub, ax, ay)
+    L0, D0 = L[:, r, r], D[:, r, r]
+    sL, sD = np.zeros_like(L0), np.zeros_like(D0)
+    rng = np.random.default_rng(i * 7919 + j)
+    for _ in range(samples if rel > 0 else 0):
+        sp = sub * (1.0 + rel * rng.choice([-1.0, 1.0], size=sub.shape) * rng.uniform(0.5, 1.0, size=sub.shape))
+        L1, D1 = oracle.operator(p, sp, ax, ay)
+        sL = np.maximum(sL, np.abs(L1[:, r, r] - L0))
+        sD = np.maximum(sD, np.abs(D1[:, r, r] - D0))
+    return L0, D0, sL, sD

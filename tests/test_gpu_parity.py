@@ -21,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2607_24325_b300 import hweno as hw  # noqa: E402
-from helpers import cfg_from, plane_rel_err, oracle_spread, within_spread    # noqa: E402
+from helpers import cfg_from, plane_rel_err, oracle_spread, within_spread, window_operator    # noqa: E402
 
 W2D = (0.99, 0.0025, 0.0025, 0.0025, 0.0025)
 TOL64 = 1e-12
@@ -570,27 +570,6 @@ def test_constant_state_is_steady(dim):
         s.close()
 
 
-def _window_operator(prob, U, i, j, ax, ay, r=3, rel=0.0, samples=4):
-    """Oracle L and D at cell (i, j) from a (2r+1)^2 window around it (the
-    operator at a cell depends on a radius-2 neighbourhood only), and their
-    absolute spread under random relative input perturbations of size `rel`
-    (the condition of that cell's outputs at the working precision)."""
-    sub = np.ascontiguousarray(U[:, j - r:j + r + 1, i - r:i + r + 1])
-    m = 2 * r + 1
-    p = oracle.Problem(dim=2, equation=prob.equation, nx=m, ny=m, xlo=0, xhi=m * prob.dx, ylo=0,
-                       yhi=m * prob.dy, lin_w=prob.lin_w, bc=(1, 1, 1, 1))
-    L, D = oracle.operator(p, sub, ax, ay)
-    L0, D0 = L[:, r, r], D[:, r, r]
-    sL, sD = np.zeros_like(L0), np.zeros_like(D0)
-    rng = np.random.default_rng(i * 7919 + j)
-    for _ in range(samples if rel > 0 else 0):
-        sp = sub * (1.0 + rel * rng.choice([-1.0, 1.0], size=sub.shape) * rng.uniform(0.5, 1.0, size=sub.shape))
-        L1, D1 = oracle.operator(p, sp, ax, ay)
-        sL = np.maximum(sL, np.abs(L1[:, r, r] - L0))
-        sD = np.maximum(sD, np.abs(D1[:, r, r] - D0))
-    return L0, D0, sL, sD
-
-
 @pytest.mark.parametrize("precision", [hw.FP64, hw.FP32_IND64])
 def test_full_size_sampled_parity(precision):
     """The bench's 4096^2 four-quadrant state, launch shape autotuned as in
@@ -627,6 +606,6 @@ def test_full_size_sampled_parity(precision):
     Dmax = np.maximum(np.abs(Dh).reshape(Dh.shape[0], -1).max(axis=1), np.concatenate([Umax, Umax]))
     tol = 1e-12 if precision == hw.FP64 else 2e-5
     for (i, j) in cells:
-        Lr, Dr, sL, sD = _window_operator(prob, Uin, i, j, ax, ay, rel=rel)
+        Lr, Dr, sL, sD = window_operator(prob, Uin, i, j, ax, ay, rel=rel)
         assert np.all(np.abs(Lh[:, j, i] - Lr) <= np.maximum(tol * Lmax, 100.0 * sL)), (i, j)
         assert np.all(np.abs(Dh[:, j, i] - Dr) <= np.maximum(tol * Dmax, 100.0 * sD)), (i, j)
