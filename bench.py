@@ -347,9 +347,11 @@ def time_steps(obj, torch, steps, flush=None, clock_gpu=0):
     return total, stage_ms / max(stage_n, 1), stage_n, launches, clk.summary()
 
 
-def roofline(algo_key, cells_per_launch, stage_ms, kind, sms, mhz, precision_name, traffic_per_cell=None):
+def roofline(algo_key, cells_per_launch, stage_ms, kind, sms, mhz, precision_name, traffic_per_cell=None,
+             probe=None):
     """The ALU roofline of the stage kernel: algorithmic flops of a launch
-    over its mean measured duration against the unit-count peak."""
+    over its mean measured duration against the unit-count peak (and against
+    the FMA microbenchmark's measured rate, `probe` in TFLOP/s)."""
     peak = alu_peak_tflops(kind, sms, mhz)
     fl = ALGO_FLOPS[algo_key]
     achieved = fl * cells_per_launch / (stage_ms * 1e-3) / 1e12
@@ -362,6 +364,10 @@ def roofline(algo_key, cells_per_launch, stage_ms, kind, sms, mhz, precision_nam
     if traffic_per_cell is not None:
         out["traffic_unit"] = "bytes per launch"
         out["traffic_note"] = TRAFFIC_NOTE
+    if probe:
+        out["peak_probe"] = probe
+        out["frac_of_probe"] = achieved / probe
+        out["probe_source"] = f"hweno_peak_fma: independent {kind.upper()} FMA chains on every SM, timed with CUDA events"
     ex = EXEC_FLOPS.get((algo_key, kind))
     if ex is not None:
         out["frac_executed"] = ex * cells_per_launch / (stage_ms * 1e-3) / 1e12 / peak
@@ -376,13 +382,16 @@ def hbm_fraction(kind, esz, cells, stage_ms, hbm_peak, hbm_src):
             "bytes_per_cell_stage": b}
 
 
-def device_facts(torch, local):
+def device_facts(torch, local, hw):
+    """SM count, clock, HBM peak, and the FMA microbenchmark's FP32 and FP64
+    rates (TFLOP/s) measured now on this GPU."""
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     mhz = float(peaks.get("sm_max_mhz") or 2032.0)
     hbm = peaks.get("hbm_gbs")
+    probe = {"f32": hw.hweno_peak_fma(hw.FP32) / 1e12, "f64": hw.hweno_peak_fma(hw.FP64) / 1e12}
     return {"sms": props.multi_processor_count, "mhz": mhz, "hbm": float(hbm or 6400.0),
-            "hbm_src": "of measured" if hbm else "of fallback"}
+            "hbm_src": "of measured" if hbm else "of fallback", "probe": probe}
 
 
 def rel_l1(a, b) -> float:
@@ -549,7 +558,7 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
     entropy-wave family), every arm timed on the same state; the FP64 arm is
     the headline."""
     torch.cuda.set_device(local)
-    dev = device_facts(torch, local)
+    dev = device_facts(torch, local, hw)
     ng = args.grid if workload == "euler2d_quadrant" else args.grid_se
     make_problem, T_cmp, data, wname = problem_factory(hw, workload, ng)
 
@@ -627,7 +636,7 @@ def run_euler2d(args, hw, torch, world, rank, local, workload):
             if workload == "euler2d_quadrant" and not r["learned"] and not r["extra"] and slab is None:
                 traffic = TRAFFIC_PER_CELL.get(name)
             roof = roofline(key, r.get("cells_local", cells_rank), r["stage_ms"], kind, dev["sms"], dev["mhz"],
-                            pname, traffic)
+                            pname, traffic, probe=dev["probe"][kind])
             if r["learned"]:
                 roof["note"] = ("effective: the plain scheme's algorithmic count; the linear path skips Steps 2-3 "
                                 "and the projections on the cells the network clears")
@@ -731,7 +740,7 @@ def run_single_grid(args, hw, torch, world, rank, local, workload, cfg_kw, U0, a
     alone after a 256 MB L2 flush when the state fits in L2); one JSON line,
     the FP64 arm the headline."""
     torch.cuda.set_device(local)
-    dev = device_facts(torch, local)
+    dev = device_facts(torch, local, hw)
     U0 = torch.from_numpy(U0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda") if flush_l2 else None
     cells = int(np.prod(U0.shape[1:]))
@@ -750,7 +759,8 @@ def run_single_grid(args, hw, torch, world, rank, local, workload, cfg_kw, U0, a
         pname = {hw.FP64: "FP64", hw.FP32: "FP32", hw.FP32_IND64: "FP32_IND64"}[prec]
         out[name] = {"value": world * cells * 3 * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
                      "dtype": DTYPE[pname],
-                     "roofline": roofline(algo_key, cells, stage_ms, kind, dev["sms"], dev["mhz"], pname),
+                     "roofline": roofline(algo_key, cells, stage_ms, kind, dev["sms"], dev["mhz"], pname,
+                                          probe=dev["probe"][kind]),
                      "hbm": hbm_fraction(fkind, 8 if kind == "f64" else 4, cells, stage_ms, dev["hbm"],
                                          dev["hbm_src"]),
                      "gpu_launches": int(launches)}
@@ -782,7 +792,7 @@ def run_batch(args, hw, torch, world, rank, local, dim):
     from paper_2607_24325_b300 import partition as PT
     from paper_2607_24325_b300 import workloads as W
     torch.cuda.set_device(local)
-    dev = device_facts(torch, local)
+    dev = device_facts(torch, local, hw)
     if dim == 1:
         B = W.riemann_batch_1d(n=256, seed=1234)
         sizes = [int(x) for x in B.sizes]
@@ -829,7 +839,8 @@ def run_batch(args, hw, torch, world, rank, local, dim):
         pname = {hw.FP64: "FP64", hw.FP32: "FP32", hw.FP32_IND64: "FP32_IND64"}[prec]
         out[name] = {"value": total_cells * 3 * args.steps / (ms_max * 1e-3), "ms_per_step": ms_max / args.steps,
                      "cells": int(total_cells), "dtype": DTYPE[pname],
-                     "roofline": roofline(algo_key, cells, stage_ms, kind, dev["sms"], dev["mhz"], pname),
+                     "roofline": roofline(algo_key, cells, stage_ms, kind, dev["sms"], dev["mhz"], pname,
+                                          probe=dev["probe"][kind]),
                      "hbm": hbm_fraction(fkind, 8 if kind == "f64" else 4, cells, stage_ms, dev["hbm"],
                                          dev["hbm_src"]),
                      "gpu_launches": int(launches), "launch_shape": list(shape)}
