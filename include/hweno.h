@@ -136,7 +136,11 @@ const char* hweno_version(void);
 /* Create a solver for one grid (Sec. 2.1 / 2.2).  cuda_stream is the
  * caller's cudaStream_t (NULL = legacy default stream) that data calls order
  * against.  Allocates the library workspace on the current device.
- * Errors: HWENO_ERR_ARG (bad config), HWENO_ERR_OOM, HWENO_ERR_CUDA. */
+ * Errors: HWENO_ERR_ARG (bad config: dim not 1 or 2, fewer than 3 cells per
+ * direction, more than 2^31 cells, an empty or non-finite domain, linear
+ * weights not positive or not summing to 1, eps, cfl, gamma_gas (Euler) or
+ * the advection speeds not finite and in range, unpaired periodic sides, an
+ * unknown enum value), HWENO_ERR_OOM, HWENO_ERR_CUDA. */
 hweno_status hweno_create(const hweno_config* cfg, void* cuda_stream, hweno_solver** out);
 /* Free the solver and its workspace (NULL is a no-op). */
 void hweno_destroy(hweno_solver* s);
@@ -375,7 +379,8 @@ typedef struct {
 hweno_status hweno_indicator_train(const float* feat, const float* dev, long long n, const hweno_train_opts* opts,
                                    const float* init_params, float* params_out, double* losses_out,
                                    void* cuda_stream);
-/* The visiting order of epoch `epoch` of hweno_indicator_train (host int[n]). */
+/* The visiting order of epoch `epoch` of hweno_indicator_train (host int[n]);
+ * does nothing when perm is NULL or n < 1. */
 void hweno_train_permutation(unsigned long long seed, int epoch, long long n, int* perm);
 
 /* ---- Allocation-free step (the paper has no counterpart: this serves

@@ -70,11 +70,17 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
     return fail(HWENO_ERR_ARG, "need at least 3 cells per direction (nx=%d ny=%d)", c->nx, c->ny);
   if ((long long)c->nx * (c->dim == 2 ? c->ny : 1) > (1LL << 31))
     return fail(HWENO_ERR_ARG, "grid too large (more than 2^31 cells)");
+  if (!std::isfinite(c->xlo) || !std::isfinite(c->xhi) ||
+      (c->dim == 2 && (!std::isfinite(c->ylo) || !std::isfinite(c->yhi))))
+    return fail(HWENO_ERR_ARG, "domain bounds must be finite");
   if (!(c->xhi > c->xlo) || (c->dim == 2 && !(c->yhi > c->ylo)))
     return fail(HWENO_ERR_ARG, "empty domain");
   if (c->equation < 0 || c->equation > 2) return fail(HWENO_ERR_ARG, "unknown equation %d", c->equation);
-  if (c->equation == HWENO_EQ_EULER && !(c->gamma_gas > 1.0))
-    return fail(HWENO_ERR_ARG, "gamma_gas must exceed 1");
+  if (c->equation == HWENO_EQ_EULER && !(c->gamma_gas > 1.0 && std::isfinite(c->gamma_gas)))
+    return fail(HWENO_ERR_ARG, "gamma_gas must be finite and exceed 1");
+  if (c->equation == HWENO_EQ_ADVECTION &&
+      (!std::isfinite(c->adv_x) || (c->dim == 2 && !std::isfinite(c->adv_y))))
+    return fail(HWENO_ERR_ARG, "advection speeds must be finite");
   const int nw = c->dim == 1 ? 3 : 5;
   double s = 0.0;
   for (int m = 0; m < nw; ++m) {
@@ -82,11 +88,11 @@ hweno_status validate(const hweno_config* c, int expect_dim) {
     s += c->lin_w[m];
   }
   if (std::fabs(s - 1.0) > 1e-12) return fail(HWENO_ERR_ARG, "linear weights must sum to 1 (sum %.17g)", s);
-  if (!(c->eps > 0.0)) return fail(HWENO_ERR_ARG, "eps must be positive");
+  if (!(c->eps > 0.0) || !std::isfinite(c->eps)) return fail(HWENO_ERR_ARG, "eps must be positive and finite");
   if (c->weight_pow != 1 && c->weight_pow != 2) return fail(HWENO_ERR_ARG, "weight_pow must be 1 or 2");
   if (c->smoothness != HWENO_BETA_MOMENT && c->smoothness != HWENO_BETA_TYPICAL)
     return fail(HWENO_ERR_ARG, "smoothness must be HWENO_BETA_MOMENT or HWENO_BETA_TYPICAL");
-  if (!(c->cfl > 0.0)) return fail(HWENO_ERR_ARG, "cfl must be positive");
+  if (!(c->cfl > 0.0) || !std::isfinite(c->cfl)) return fail(HWENO_ERR_ARG, "cfl must be positive and finite");
   if (c->dt_rule != HWENO_DT_CFL && c->dt_rule != HWENO_DT_CFL_DX53) return fail(HWENO_ERR_ARG, "bad dt_rule");
   if (c->precision != HWENO_FP64 && c->precision != HWENO_FP32 && c->precision != HWENO_FP32_IND64)
     return fail(HWENO_ERR_ARG, "bad precision");
@@ -131,6 +137,17 @@ namespace hw {
 hweno_status report_error(hweno_status st, const char* msg) { return fail(st, "%s", msg); }
 hweno_status check_config(const hweno_config* cfg, int expect_dim) { return validate(cfg, expect_dim); }
 }  // namespace hw
+
+// A device buffer or an event owned by one scope: released on every return
+// path, the error returns of HW_CK included.
+struct ScopedDev {
+  void* p = nullptr;
+  ~ScopedDev() { if (p) cudaFree(p); }
+};
+struct ScopedEvent {
+  cudaEvent_t e = nullptr;
+  ~ScopedEvent() { if (e) cudaEventDestroy(e); }
+};
 
 // One engine serves both a single grid (n_inst = 1) and a 1D batch.
 struct Engine {
@@ -697,12 +714,12 @@ struct Engine {
         cand.push_back(s);
       }
     }
-    void *L = nullptr, *D = nullptr;
-    HW_CK(cudaMalloc(&L, (size_t)cells * esz * nf));
-    HW_CK(cudaMalloc(&D, (size_t)cells * esz * nd));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    HW_CK(cudaEventCreate(&e0));
-    HW_CK(cudaEventCreate(&e1));
+    ScopedDev L, D;
+    HW_CK(cudaMalloc(&L.p, (size_t)cells * esz * nf));
+    HW_CK(cudaMalloc(&D.p, (size_t)cells * esz * nd));
+    ScopedEvent e0, e1;
+    HW_CK(cudaEventCreate(&e0.e));
+    HW_CK(cudaEventCreate(&e1.e));
     std::vector<double> a0(2 * n_inst, 1.0);
     if (dim == 1 || batch2) HW_CK(cudaMemcpy(alpha_op, a0.data(), sizeof(double) * a0.size(), cudaMemcpyHostToDevice));
     const hw::LaunchShape keep = shape;
@@ -711,22 +728,18 @@ struct Engine {
     hweno_status st = HWENO_OK;
     for (const hw::LaunchShape& c : cand) {
       shape = c;
-      st = stage(0, S, L, ctl, 1.0, 1.0, D);  // warm-up
+      st = stage(0, S, L.p, ctl, 1.0, 1.0, D.p);  // warm-up
       if (st != HWENO_OK) break;
-      cudaEventRecord(e0, own);
-      for (int r = 0; r < reps && st == HWENO_OK; ++r) st = stage(0, S, L, ctl, 1.0, 1.0, D);
-      cudaEventRecord(e1, own);
+      cudaEventRecord(e0.e, own);
+      for (int r = 0; r < reps && st == HWENO_OK; ++r) st = stage(0, S, L.p, ctl, 1.0, 1.0, D.p);
+      cudaEventRecord(e1.e, own);
       if (st != HWENO_OK) break;
-      cudaEventSynchronize(e1);
+      cudaEventSynchronize(e1.e);
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventElapsedTime(&ms, e0.e, e1.e);
       if (ms < best) { best = ms; pick = c; }
     }
     shape = st == HWENO_OK ? pick : keep;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(L);
-    cudaFree(D);
     if (st != HWENO_OK) return st;
     if (best_ms) *best_ms = best / reps;
     drop_graph();
@@ -1119,6 +1132,7 @@ static unsigned long long splitmix64(unsigned long long& state) {
 }
 
 void hweno_train_permutation(unsigned long long seed, int epoch, long long n, int* perm) {
+  if (!perm || n < 1) return;
   unsigned long long st = seed + (unsigned long long)(epoch + 1) * 0xD1B54A32D192ED03ull;
   for (long long i = 0; i < n; ++i) perm[i] = (int)i;
   for (long long i = n - 1; i > 0; --i) {

@@ -77,6 +77,11 @@ BAD = [
     (dict(bc=(hw.BC_SPLIT, hw.BC_OUTFLOW, 0, 0)), "2D grid"),
     (dict(bc=(hw.BC_OUTFLOW, 6, 0, 0)), "boundary"),
     (dict(smoothness=2), "smoothness"),
+    (dict(xhi=float("inf")), "finite"),
+    (dict(eps=float("inf")), "eps"),
+    (dict(cfl=float("nan")), "cfl"),
+    (dict(equation=hw.EQ_EULER, gamma_gas=float("inf")), "gamma_gas"),
+    (dict(adv_x=float("nan")), "advection speeds"),
 ]
 
 
