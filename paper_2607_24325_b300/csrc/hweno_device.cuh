@@ -94,13 +94,16 @@ __device__ __forceinline__ T beta_typical_1d(T c1, T c2, T c3, T c4) {
          T(87617.0 / 140.0) * c4 * c4;
 }
 
-template <typename T>
-__device__ __forceinline__ T fabs_t(T x) { return x < T(0) ? -x : x; }
+// |x| by clearing the sign bit (a free operand modifier of the consuming
+// add; a compare-and-negate would issue on the FP64 pipe in FP64).
+__device__ __forceinline__ double fabs_t(double x) { return fabs(x); }
+__device__ __forceinline__ float fabs_t(float x) { return fabsf(x); }
 
-// Reciprocal and quotient: IEEE in FP64; in FP32 the fast approximate forms
-// (a few ulp), far below the FP32 stencil's own conditioning.
-// FP32: the hardware approximate reciprocal (PTX rcp.approx.ftz.f32, about
-// 1 ulp) and a quotient as a times that reciprocal.
+// Reciprocal and quotient.  FP64: the reciprocal by Newton-Raphson from an
+// FP32 seed (rcp64 below, faithful), the quotient IEEE.  FP32: the fast
+// approximate forms (a few ulp), far below the FP32 stencil's own
+// conditioning -- the hardware approximate reciprocal (PTX
+// rcp.approx.ftz.f32, about 1 ulp) and a quotient as a times it.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -125,8 +128,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_t(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double div_t(double a, double b) { return a / b; }
 __device__ __forceinline__ float div_t(float a, float b) { return a * rcp_approx(b); }
 // Square root in the argument's own precision (an unqualified sqrt of a
@@ -189,6 +190,27 @@ __device__ __forceinline__ double rcp_newton(double s) {
   return fma(y, fma(-s, y, 1.0), y);
 }
 
+// 1/s in FP64, faithful (within one unit in the last place) wherever s and
+// 1/s are normal numbers: Newton-Raphson for the reciprocal,
+// y <- y + y (1 - s y) with the residual formed by one fused multiply-add
+// (Markstein), twice from the hardware's approximate FP64 reciprocal (PTX
+// rcp.approx.ftz.f64, about the leading 20 bits); each step squares the
+// relative error, so the second leaves only the rounding of its last
+// operation.  Four FP64 operations, no branch.  Zeros, infinities and NaN
+// keep the approximation's IEEE results (+-inf, +-0, NaN); subnormal
+// arguments and results are flushed (1/s = +-inf, 0), as the approximation
+// does.
+__device__ __forceinline__ double rcp64(double s) {
+  double y0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(s));
+  const unsigned e = ((unsigned)__double2hiint(s) >> 20) & 0x7ffu;
+  double y = fma(y0, fma(-s, y0, 1.0), y0);
+  y = fma(y, fma(-s, y, 1.0), y);
+  return e - 1u < 2045u ? y : y0;
+}
+__device__ __forceinline__ double rcp_t(double x) { return rcp64(x); }
+__device__ __forceinline__ float rcp_t(float x) { return rcp_approx(x); }
+
 // Input conversion of the coefficient maps: identity, or the exact widening.
 template <typename TC, typename TQ>
 __device__ __forceinline__ TC to_tc(TQ x) {
@@ -200,8 +222,10 @@ __device__ __forceinline__ TC to_tc(TQ x) {
 // one target polynomial and NL linear ones: given beta_0..beta_NL and tau,
 // returns r = omega_0 / gamma_0 and omega_1..omega_NL (om[0] unused).
 // w~_m = gamma_m (1 + tau^2/d_m), d_m = beta_m^{1|2} + eps, omega = w~ / sum w~.
-// FP64 uses the equal form w~_m prod_k d_k = gamma_m (d_m + tau^2) prod_{k!=m} d_k,
-// which needs one division instead of NL+2 (FP64 division is costly on B300);
+// FP64 scales every w~_m by P = prod_k d_k: with Q_m = prod_{k!=m} d_k
+// (prefix times suffix products), w~_m P = gamma_m f_m, f_m = P + tau^2 Q_m
+// (one fused multiply-add), so the weights need one reciprocal instead of
+// NL+2 (FP64 division is costly on B300) and r = f_0 / sum_m gamma_m f_m;
 // FP32 keeps the quotients (products of d could overflow its range).
 template <typename T, int NL>
 __device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<T>& w, T& r, T* om) {
@@ -209,28 +233,40 @@ __device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<
   T d[NL + 1];
 #pragma unroll
   for (int m = 0; m <= NL; ++m) d[m] = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
-  T e[NL + 1];
   if constexpr (sizeof(T) == 8) {
     T pre[NL + 1], suf[NL + 1];
-    pre[0] = T(1);
+    pre[1] = d[0];
 #pragma unroll
-    for (int m = 1; m <= NL; ++m) pre[m] = pre[m - 1] * d[m - 1];
-    suf[NL] = T(1);
+    for (int m = 2; m <= NL; ++m) pre[m] = pre[m - 1] * d[m - 1];
+    suf[NL - 1] = d[NL];
 #pragma unroll
-    for (int m = NL - 1; m >= 0; --m) suf[m] = suf[m + 1] * d[m + 1];
+    for (int m = NL - 2; m >= 0; --m) suf[m] = suf[m + 1] * d[m + 1];
+    const T P = d[0] * suf[0];
+    T f[NL + 1];
 #pragma unroll
-    for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (d[m] + t2) * (pre[m] * suf[m]);
+    for (int m = 0; m <= NL; ++m) {
+      const T q = m == 0 ? suf[0] : (m == NL ? pre[NL] : pre[m] * suf[m]);
+      f[m] = fma(t2, q, P);
+    }
+    T s = w.g[0] * f[0];
+#pragma unroll
+    for (int m = 1; m <= NL; ++m) s = fma(w.g[m], f[m], s);
+    const T inv = rcp_t(s);
+    r = f[0] * inv;
+#pragma unroll
+    for (int m = 1; m <= NL; ++m) om[m] = (w.g[m] * f[m]) * inv;
   } else {
+    T e[NL + 1];
 #pragma unroll
     for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (T(1) + div_t(t2, d[m]));
+    T s = e[0];
+#pragma unroll
+    for (int m = 1; m <= NL; ++m) s += e[m];
+    const T inv = rcp_t(s);
+    r = e[0] * inv * w.inv_g0;
+#pragma unroll
+    for (int m = 1; m <= NL; ++m) om[m] = e[m] * inv;
   }
-  T s = e[0];
-#pragma unroll
-  for (int m = 1; m <= NL; ++m) s += e[m];
-  const T inv = rcp_t(s);
-  r = e[0] * inv * w.inv_g0;
-#pragma unroll
-  for (int m = 1; m <= NL; ++m) om[m] = e[m] * inv;
 }
 
 // ---------------------------------------------------------------------------
@@ -363,6 +399,7 @@ __device__ __forceinline__ Rec1<T> recon1(T um, T u0, T up, T vm, T vp, T dx, T 
 template <typename T>
 struct Eig {
   T u, v, c, H, q2h, hb1, hic;  // q2h = (u^2+v^2)/2, hb1 = (g-1)/(2c^2), hic = 1/(2c)
+  T qH;                         // q2h - H
 };
 
 template <typename T>
@@ -379,6 +416,7 @@ __device__ __forceinline__ Eig<T> eig1(T r, T m, T E, T g) {
   e.hic = T(0.5) * ic;
   e.H = (E + p) * ir;
   e.hb1 = (T(0.5) * (g - T(1))) * ic * ic;
+  e.qH = e.q2h - e.H;
   return e;
 }
 
@@ -396,6 +434,7 @@ __device__ __forceinline__ Eig<T> eig2(T r, T mx, T my, T E, T g) {
   e.hic = T(0.5) * ic;
   e.H = (E + p) * ir;
   e.hb1 = (T(0.5) * (g - T(1))) * ic * ic;
+  e.qH = e.q2h - e.H;
   return e;
 }
 
@@ -417,19 +456,21 @@ __device__ __forceinline__ void r1_apply(const Eig<T>& e, const T* w, T* y) {
   const T dif = w[2] - w[0];
   y[0] = sum;
   y[1] = e.u * sum + e.c * dif;
-  y[2] = e.H * (w[0] + w[2]) + e.q2h * w[1] + e.u * e.c * dif;
+  y[2] = e.H * sum + e.qH * w[1] + e.u * e.c * dif;  // H (w0 + w2) + q2h w1
 }
 
-// 2D, direction D (0: x, 1: y): w = L_D x.
+// 2D, direction D (0: x, 1: y): w = L_D x.  With s = E + q2h rho - u m_x -
+// v m_y (three fused multiply-adds) and t = u_n rho - m_n:
+// w = (hb1 s + hic t, rho - 2 hb1 s, m_t - u_t rho, hb1 s - hic t).
 template <int D, typename T>
 __device__ __forceinline__ void l2_apply(const Eig<T>& e, const T* x, T* w) {
-  const T sh = e.hb1 * (e.q2h * x[0] - e.u * x[1] - e.v * x[2] + x[3]);  // half of s
+  const T sh = e.hb1 * (x[3] + e.q2h * x[0] - e.u * x[1] - e.v * x[2]);  // half of s
   const T un = D == 0 ? e.u : e.v;
-  const T th = (un * x[0] - x[1 + D]) * e.hic;                              // half of t
-  w[0] = sh + th;
+  const T t = un * x[0] - x[1 + D];
+  w[0] = sh + e.hic * t;
   w[1] = x[0] - T(2) * sh;
   w[2] = D == 0 ? x[2] - e.v * x[0] : x[1] - e.u * x[0];
-  w[3] = sh - th;
+  w[3] = sh - e.hic * t;
 }
 // 2D, direction D: y = R_D w.
 template <int D, typename T>
@@ -446,53 +487,70 @@ __device__ __forceinline__ void r2_apply(const Eig<T>& e, const T* w, T* y) {
     y[1] = e.u * sum + w[2];
     y[2] = e.v * sum + e.c * dif;
   }
-  y[3] = e.H * (w[0] + w[3]) + e.q2h * w[1] + ut * w[2] + un * e.c * dif;
+  // H (w0 + w3) + q2h w1 = H sum + (q2h - H) w1
+  y[3] = e.H * sum + e.qH * w[1] + ut * w[2] + un * e.c * dif;
 }
 
-// Flux f(U) and its directional derivative f'(U) V, 1D Euler.
+// Flux f(U) and its directional derivative f'(U) V, 1D Euler.  With
+// u = m / rho, H = (E + p) / rho and t = V_m - u V_rho (so that rho du = t):
+//   f'(U) V = (V_m,  u (V_m + t) + dp,  H t + u (V_E + dp)),
+//   dp = (g - 1) (V_E - u V_m + u^2/2 V_rho);
+// no division by rho beyond the one reciprocal.
 template <typename T>
 __device__ __forceinline__ void euler1_flux(const T* U, const T* V, T g, T* F, T* H) {
   const T ir = rcp_t(U[0]);
   const T u = U[1] * ir;
-  const T p = (g - T(1)) * (U[2] - T(0.5) * U[1] * u);
+  const T gm = g - T(1);
+  const T ek = T(0.5) * (u * u);
+  const T p = gm * (U[2] - U[0] * ek);
+  const T Ep = U[2] + p;
   F[0] = U[1];
   F[1] = U[1] * u + p;
-  F[2] = u * (U[2] + p);
-  const T du = (V[1] - u * V[0]) * ir;
-  const T dp = (g - T(1)) * (V[2] - u * V[1] + T(0.5) * u * u * V[0]);
+  F[2] = u * Ep;
+  const T h = Ep * ir;
+  const T t = V[1] - u * V[0];
+  const T dp = gm * (V[2] - u * V[1] + ek * V[0]);
   H[0] = V[1];
-  H[1] = T(2) * u * V[1] - u * u * V[0] + dp;
-  H[2] = du * (U[2] + p) + u * (V[2] + dp);
+  H[1] = u * (V[1] + t) + dp;
+  H[2] = h * t + u * (V[2] + dp);
 }
 
 // 2D Euler, direction D: flux and directional derivatives along V and W.
+// With u_n the normal velocity, H = (E + p) / rho and t = V_{m_n} - u_n V_rho
+// (rho d(u_n) = t, rho d(u_t) = V_{m_t} - u_t V_rho):
+//   d(m_n u_n + p) = u_n (V_{m_n} + t) + dp,  d(m_n u_t) = u_t t + u_n V_{m_t},
+//   d(u_n (E + p)) = H t + u_n (V_E + dp),
+//   dp = (g - 1) (V_E - u V_{m_x} - v V_{m_y} + |u|^2/2 V_rho).
 template <int D, typename T>
 __device__ __forceinline__ void euler2_flux(const T* U, const T* V, const T* Wv, T g, T* F, T* HV,
                                             T* HW) {
   const T ir = rcp_t(U[0]);
   const T u = U[1] * ir, v = U[2] * ir;
   const T gm = g - T(1);
-  const T p = gm * (U[3] - T(0.5) * (U[1] * u + U[2] * v));
+  const T ek = T(0.5) * (u * u + v * v);
+  const T p = gm * (U[3] - U[0] * ek);
+  const T Ep = U[3] + p;
   const T un = D == 0 ? u : v;
+  const T ut = D == 0 ? v : u;
   const T mn = U[1 + D];
   F[0] = mn;
-  F[1] = mn * u + (D == 0 ? p : T(0));
-  F[2] = mn * v + (D == 1 ? p : T(0));
-  F[3] = un * (U[3] + p);
-  const T ek = T(0.5) * (u * u + v * v);
+  F[1] = D == 0 ? mn * u + p : mn * u;
+  F[2] = D == 1 ? mn * v + p : mn * v;
+  F[3] = un * Ep;
+  const T h = Ep * ir;
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
     const T* X = s == 0 ? V : Wv;
     T* Hh = s == 0 ? HV : HW;
-    const T du = (X[1] - u * X[0]) * ir;
-    const T dv = (X[2] - v * X[0]) * ir;
+    const T dmn = X[1 + D], dmt = X[2 - D];
+    const T t = dmn - un * X[0];
     const T dp = gm * (X[3] - u * X[1] - v * X[2] + ek * X[0]);
-    const T dmn = X[1 + D];
-    const T dun = D == 0 ? du : dv;
+    const T hn = un * (dmn + t) + dp;  // normal momentum flux
+    const T ht = ut * t + un * dmt;    // tangential momentum flux
     Hh[0] = dmn;
-    Hh[1] = dmn * u + mn * du + (D == 0 ? dp : T(0));
-    Hh[2] = dmn * v + mn * dv + (D == 1 ? dp : T(0));
-    Hh[3] = dun * (U[3] + p) + un * (X[3] + dp);
+    Hh[1 + D] = hn;
+    Hh[2 - D] = ht;
+    Hh[3] = h * t + un * (X[3] + dp);
   }
 }
 

@@ -228,16 +228,30 @@ __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
   const TC s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
   const TC s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
   TC* c = o.c;
-  if constexpr (C0) {
-    c[0] = q5 + (TC(5) * sc - TC(292) * (ex + ey) + TC(81) * (m1110 + m1716)) * TC(1.0 / 2880.0);
+  if constexpr (sizeof(TC) == 8) {
+    // FP64: the denominators folded into the constants (one multiply fewer
+    // per coefficient; the constants' own rounding is far below 1e-15)
+    if constexpr (C0) {
+      c[0] = q5 + TC(5.0 / 2880.0) * sc - TC(292.0 / 2880.0) * (ex + ey) + TC(81.0 / 2880.0) * (m1110 + m1716);
+    } else {
+      c[0] = TC(0);
+    }
+    c[1] = TC(1.0 / 12.0) * ax + TC(19.0 / 24.0) * dxe - TC(0.25) * s1011 + TC(0.125) * s1213;
+    c[2] = TC(1.0 / 12.0) * ay + TC(19.0 / 24.0) * dye + TC(0.125) * s1415 - TC(0.25) * s1617;
+    c[3] = TC(1.0 / 24.0) * ey + TC(31.0 / 24.0) * ex - TC(1.0 / 48.0) * sc - TC(0.375) * m1110;
+    c[5] = TC(1.0 / 24.0) * ex + TC(31.0 / 24.0) * ey - TC(1.0 / 48.0) * sc - TC(0.375) * m1716;
   } else {
-    c[0] = TC(0);
+    if constexpr (C0) {
+      c[0] = q5 + (TC(5) * sc - TC(292) * (ex + ey) + TC(81) * (m1110 + m1716)) * TC(1.0 / 2880.0);
+    } else {
+      c[0] = TC(0);
+    }
+    c[1] = (TC(2) * ax + TC(19) * dxe - TC(6) * s1011 + TC(3) * s1213) * TC(1.0 / 24.0);
+    c[2] = (TC(2) * ay + TC(19) * dye + TC(3) * s1415 - TC(6) * s1617) * TC(1.0 / 24.0);
+    c[3] = (TC(2) * ey + TC(62) * ex - sc - TC(18) * m1110) * TC(1.0 / 48.0);
+    c[5] = (TC(2) * ex + TC(62) * ey - sc - TC(18) * m1716) * TC(1.0 / 48.0);
   }
-  c[1] = (TC(2) * ax + TC(19) * dxe - TC(6) * s1011 + TC(3) * s1213) * TC(1.0 / 24.0);
-  c[2] = (TC(2) * ay + TC(19) * dye + TC(3) * s1415 - TC(6) * s1617) * TC(1.0 / 24.0);
-  c[3] = (TC(2) * ey + TC(62) * ex - sc - TC(18) * m1110) * TC(1.0 / 48.0);
   c[4] = TC(-0.375) * cx - TC(0.625) * (m1213 + m1415);
-  c[5] = (TC(2) * ex + TC(62) * ey - sc - TC(18) * m1716) * TC(1.0 / 48.0);
   c[6] = (TC(4) * (s1011 - dxe) - ax - TC(2) * s1213) * TC(0.05);
   c[7] = TC(-0.25) * ay - TC(0.5) * dye;
   c[8] = TC(-0.25) * ax - TC(0.5) * dxe;
@@ -310,10 +324,18 @@ __device__ __forceinline__ void combine2(const Coef2<T>& k, T r, const T* om, co
   const T gs = (w.g[1] + w.g[2]) + (w.g[3] + w.g[4]);
   const T ws = (om[1] + om[2]) + (om[3] + om[4]);
   cu[0] = r * (c[0] - gs * k.q5) + ws * k.q5;
-  cu[1] = r * (c[1] - ((w.g[1] + w.g[4]) * k.dW + (w.g[2] + w.g[3]) * k.dE)) +
-          ((om[1] + om[4]) * k.dW + (om[2] + om[3]) * k.dE);
-  cu[2] = r * (c[2] - ((w.g[1] + w.g[2]) * k.dS + (w.g[3] + w.g[4]) * k.dN)) +
-          ((om[1] + om[2]) * k.dS + (om[3] + om[4]) * k.dN);
+  if constexpr (sizeof(T) == 8) {
+    // r (c_1 - G_W dW - G_E dE) + O_W dW + O_E dE = r c_1 + (O_W - r G_W) dW + (O_E - r G_E) dE
+    const T aW = (om[1] + om[4]) - r * (w.g[1] + w.g[4]), aE = (om[2] + om[3]) - r * (w.g[2] + w.g[3]);
+    const T aS = (om[1] + om[2]) - r * (w.g[1] + w.g[2]), aN = (om[3] + om[4]) - r * (w.g[3] + w.g[4]);
+    cu[1] = r * c[1] + (aW * k.dW + aE * k.dE);
+    cu[2] = r * c[2] + (aS * k.dS + aN * k.dN);
+  } else {
+    cu[1] = r * (c[1] - ((w.g[1] + w.g[4]) * k.dW + (w.g[2] + w.g[3]) * k.dE)) +
+            ((om[1] + om[4]) * k.dW + (om[2] + om[3]) * k.dE);
+    cu[2] = r * (c[2] - ((w.g[1] + w.g[2]) * k.dS + (w.g[3] + w.g[4]) * k.dN)) +
+            ((om[1] + om[2]) * k.dS + (om[3] + om[4]) * k.dN);
+  }
 #pragma unroll
   for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
 }
@@ -526,9 +548,11 @@ __device__ __forceinline__ void finish2(const float* a, const WeightsT<float>& w
 }
 
 // Values at the three Gauss points of the face xi = +-1/2 (sgn = +1 / -1)
-// of the pass frame: u, d/dxi u, d/deta u.
+// of the pass frame: u, d/dxi u, d/deta u; and the face averages of the
+// three (the 3-point Gauss rule is exact for these degree-4 restrictions:
+// over eta in [-1/2, 1/2], eta^2 averages 1/12 and eta^4 1/80).
 template <typename T>
-struct FacePts { T u[3], un[3], ut[3]; };
+struct FacePts { T u[3], un[3], ut[3], au, an, at; };
 
 template <typename T>
 __device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
@@ -548,6 +572,9 @@ __device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
   o.u[0] = ue - uo; o.u[1] = A0; o.u[2] = ue + uo;
   o.un[0] = ne - no; o.un[1] = B0; o.un[2] = ne + no;
   o.ut[0] = te - to; o.ut[1] = A1; o.ut[2] = te + to;
+  o.au = A0 + A2 * T(1.0 / 12.0) + A4 * T(0.0125);
+  o.an = B0 + B2 * T(1.0 / 12.0);
+  o.at = A1 + T(0.25) * A3;
 }
 
 }  // namespace hw

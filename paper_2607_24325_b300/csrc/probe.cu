@@ -1,8 +1,8 @@
 // probe.cu -- measured FMA throughput of this GPU (the ALU roofline the
 // stencil kernels are compared against): a grid of 8 resident CTAs per SM,
 // each thread running 8 independent FMA chains, timed with CUDA events.
-// Also the self-check of the integer-ALU FP32 <-> FP64 conversions that the
-// mixed-precision path uses.
+// Also the self-checks of the integer-ALU FP32 <-> FP64 conversions that the
+// mixed-precision path uses and of the FP64 reciprocal of the FP64 kernels.
 #include <cuda_runtime.h>
 
 #include "hweno.h"
@@ -59,7 +59,20 @@ __global__ void k_convert_check(const float* f, double* wide, const double* d, f
   }
 }
 
+__global__ void k_rcp64_check(const double* x, double* y, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = hw::rcp64(x[i]);
+}
+
 }  // namespace
+
+extern "C" hweno_status hweno_selftest_rcp64(const double* x_in, double* y_out, int n) {
+  if (n < 0 || (n > 0 && (!x_in || !y_out))) return HWENO_ERR_ARG;
+  if (n == 0) return HWENO_OK;
+  k_rcp64_check<<<(n + 255) / 256, 256>>>(x_in, y_out, n);
+  if (cudaGetLastError() != cudaSuccess) return HWENO_ERR_CUDA;
+  return cudaDeviceSynchronize() == cudaSuccess ? HWENO_OK : HWENO_ERR_CUDA;
+}
 
 extern "C" hweno_status hweno_selftest_convert(const float* f_in, double* wide_out, const double* d_in,
                                                float* narrow_out, int n) {

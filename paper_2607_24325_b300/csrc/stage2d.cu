@@ -26,11 +26,14 @@ namespace hw {
 
 static_assert(kT2 == kTile2, "host tile table and kernel tile size differ");
 
-// Lax-Friedrichs fluxes of the pass-frame x physics at one point, doubled:
-// 2 f, 2 f'(u) v (normal moment), 2 f'(u) w (tangential moment).
+// The central part of the Lax-Friedrichs fluxes of the pass-frame x physics
+// at one point, doubled: f(u-) + f(u+), f'(u-) v- + f'(u+) v+ (normal
+// moment), f'(u-) w- + f'(u+) w+ (tangential moment).  The dissipative part
+// -alpha (u+ - u-) is linear in the states, so its Gauss sum over a face is
+// formed once from the face averages (pass2d).
 template <typename T, int NC, int EQ>
 __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, const T* Up, const T* Vp,
-                                         const T* Wp, T alpha, T g, T adv, T* fu, T* fv, T* fw) {
+                                         const T* Wp, T g, T adv, T* fu, T* fv, T* fw) {
   T Fm[NC], Fp[NC], HVm[NC], HVp[NC], HWm[NC], HWp[NC];
   if constexpr (EQ == HWENO_EQ_EULER) {
     euler2_flux<0>(Um, Vm, Wm, g, Fm, HVm, HWm);
@@ -42,12 +45,12 @@ __device__ __forceinline__ void lf_point(const T* Um, const T* Vm, const T* Wm, 
     Fm[0] = adv * Um[0]; HVm[0] = adv * Vm[0]; HWm[0] = adv * Wm[0];
     Fp[0] = adv * Up[0]; HVp[0] = adv * Vp[0]; HWp[0] = adv * Wp[0];
   }
-  // twice the flux: the 1/2 is folded into the Gauss weights by the caller
+  // twice the central flux: the 1/2 is folded into the Gauss weights by the caller
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    fu[k] = (Fm[k] + Fp[k]) - alpha * (Up[k] - Um[k]);
-    fv[k] = (HVm[k] + HVp[k]) - alpha * (Vp[k] - Vm[k]);
-    fw[k] = (HWm[k] + HWp[k]) - alpha * (Wp[k] - Wm[k]);
+    fu[k] = Fm[k] + Fp[k];
+    fv[k] = HVm[k] + HVp[k];
+    fw[k] = HWm[k] + HWp[k];
   }
 }
 
@@ -274,15 +277,21 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
       }
     }
   }
-#pragma unroll
-  for (int k = 0; k < NC; ++k) { Fu[k] = T(0); Fv[k] = T(0); Fw[k] = T(0); vh[k] = T(0); }
-  const T sig[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
-  const T hsig[3] = {T(5.0 / 36.0), T(8.0 / 36.0), T(5.0 / 36.0)};  // with lf_point's 1/2
+  const T hsig[3] = {T(5.0 / 36.0), T(8.0 / 36.0), T(5.0 / 36.0)};  // Gauss weights with lf_point's 1/2
   FacePts<T> fr[NC], fl[NC];
+  // The dissipation over the low face, -(alpha / 2) times the face average
+  // of (u+ - u-) (the Gauss sum of the pointwise terms, exact for these
+  // restrictions), starts the flux sums; v-hat is the face average of
+  // u(right) - u(left) (Gauss weights summing to 1).
+  const T ha = T(0.5) * alpha;
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     face_points<T>(cu[k], T(1), fr[k]);
     face_points<T>(cu[k], T(-1), fl[k]);
+    Fu[k] = -ha * (fl[k].au - __shfl_up_sync(HW_FULL_MASK, fr[k].au, 1));
+    Fv[k] = -ha * (fl[k].an - __shfl_up_sync(HW_FULL_MASK, fr[k].an, 1));
+    Fw[k] = -ha * (fl[k].at - __shfl_up_sync(HW_FULL_MASK, fr[k].at, 1));
+    vh[k] = fr[k].au - fl[k].au;
   }
 #pragma unroll
   for (int mu = 0; mu < 3; ++mu) {
@@ -312,13 +321,12 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
       Wm[k] = __shfl_up_sync(HW_FULL_MASK, WR[k], 1);
     }
     T fu[NC], fv[NC], fw[NC];
-    lf_point<T, NC, EQ>(Um, Vm, Wm, UL, VL, WL, alpha, g, adv, fu, fv, fw);
+    lf_point<T, NC, EQ>(Um, Vm, Wm, UL, VL, WL, g, adv, fu, fv, fw);
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       Fu[k] += hsig[mu] * fu[k];
       Fv[k] += hsig[mu] * fv[k];
       Fw[k] += hsig[mu] * fw[k];
-      vh[k] += sig[mu] * (UR[k] - UL[k]);
     }
   }
 #pragma unroll

@@ -38,7 +38,7 @@ EXPORTS = (
     "hweno_last_error", "hweno_version", "hweno_create", "hweno_destroy", "hweno_stream",
     "hweno_shape", "hweno_set_state", "hweno_get_state", "hweno_alpha", "hweno_apply_operator",
     "hweno_step", "hweno_advance", "hweno_set_profiling", "hweno_profile", "hweno_peak_fma",
-    "hweno_selftest_convert",
+    "hweno_selftest_convert", "hweno_selftest_rcp64",
     "hweno_batch_create", "hweno_batch_destroy",
     "hweno_batch_stream", "hweno_batch_layout", "hweno_batch_set_state", "hweno_batch_get_state",
     "hweno_batch_advance", "hweno_batch_apply_operator", "hweno_step_1d_noalloc",
@@ -170,6 +170,7 @@ def load():
     L.hweno_profile.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
     L.hweno_peak_fma.argtypes = [C.c_int, C.POINTER(C.c_double)]
     L.hweno_selftest_convert.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.hweno_selftest_rcp64.argtypes = [vp, vp, C.c_int]
     L.hweno_batch_create.argtypes = [C.c_int, cp, vp, C.POINTER(vp)]
     L.hweno_batch_destroy.argtypes = [vp]
     L.hweno_batch_destroy.restype = None
@@ -347,6 +348,18 @@ def hweno_selftest_convert(f_in, d_in):
     narrow = torch.empty(n, dtype=torch.float32, device=f_in.device)
     _check(load().hweno_selftest_convert(f_in.data_ptr(), wide.data_ptr(), d_in.data_ptr(), narrow.data_ptr(), n))
     return wide, narrow
+
+
+def hweno_selftest_rcp64(x_in):
+    """x_in: float64 device tensor; returns 1 / x_in as the library's FP64
+    kernels compute the reciprocal."""
+    import torch
+    if x_in.dtype != torch.float64:
+        raise ValueError("x_in float64")
+    x_in = x_in.contiguous()
+    y = torch.empty_like(x_in)
+    _check(load().hweno_selftest_rcp64(x_in.data_ptr(), y.data_ptr(), x_in.numel()))
+    return y
 
 
 def hweno_batch_create(cfgs, stream=None):

@@ -69,3 +69,38 @@ def test_conversions_match_ieee():
 def test_conversion_rejects_bad_args():
     with pytest.raises(Exception):
         hw.hweno_selftest_convert(torch.zeros(3, device="cuda"), torch.zeros(4, dtype=torch.float64, device="cuda"))
+
+
+def test_rcp64_faithful():
+    """The FP64 kernels' reciprocal (Newton-Raphson from the hardware's
+    approximate FP64 reciprocal) is within one unit in the last place of the
+    correctly rounded 1/x (numpy's IEEE division) wherever x and 1/x are
+    normal, of either sign; zeros, infinities and NaN give IEEE's results,
+    subnormal arguments and results are flushed (+-inf, +-0)."""
+    rng = np.random.default_rng(11)
+    sig = rng.uniform(1.0, 2.0, 400_000)
+    x = np.ldexp(sig, rng.integers(-1022, 1023, sig.size)) * rng.choice([-1.0, 1.0], sig.size)
+    # next to powers of two, and a fine walk over one binade's significands
+    p2 = np.ldexp(1.0, np.arange(-1022, 1023, 3))
+    walk = 1.0 + np.arange(1, 8192) * 2.0 ** -13 + rng.uniform(-1, 1, 8191) * 2.0 ** -40
+    edge = np.concatenate([np.nextafter(p2, 0.0), p2, np.nextafter(p2, np.inf), walk])
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 5e-324, -5e-324, 2.2250738585072009e-308,
+                        2.2250738585072014e-308, -2.2250738585072014e-308, 4.450147717014403e-308,
+                        1.7976931348623157e308, -1.7976931348623157e308, 8.98846567431158e307,
+                        4.49423283715579e307, 1.0, -1.0, 0.1, 3.0, 1.4])
+    x = np.concatenate([special, edge, -edge, x])
+    y = hw.hweno_selftest_rcp64(torch.from_numpy(x).cuda()).cpu().numpy()
+    tiny = 2.2250738585072014e-308
+    with np.errstate(divide="ignore", over="ignore"):
+        ref = 1.0 / x
+    ref = np.where(np.abs(x) < tiny, np.copysign(np.inf, x), ref)            # subnormal argument
+    ref = np.where((np.abs(ref) < tiny) & (ref != 0), np.copysign(0.0, ref), ref)  # subnormal result
+    both_nan = np.isnan(y) & np.isnan(ref)
+    same_sign = np.signbit(y) == np.signbit(ref)
+    ulps = np.abs(y.view(np.int64) - ref.view(np.int64))
+    ok = both_nan | (same_sign & (ulps <= 1))
+    assert ok.all(), (x[~ok][:6], y[~ok][:6], ref[~ok][:6])
+    # exactly representable quotients (powers of two, +-1) and the special values are exact
+    exact = np.isin(np.arange(x.size), np.arange(special.size)) & ~np.isin(x, [0.1, 3.0, 1.4])
+    assert (both_nan | (ulps == 0))[exact].all()
+    assert (ulps[~np.isnan(ref)] == 0).mean() > 0.9
