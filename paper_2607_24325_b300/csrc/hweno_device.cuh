@@ -224,30 +224,36 @@ __device__ __forceinline__ TC to_tc(TQ x) {
 // w~_m = gamma_m (1 + tau^2/d_m), d_m = beta_m^{1|2} + eps, omega = w~ / sum w~.
 // FP64 scales every w~_m by P = prod_k d_k: with Q_m = prod_{k!=m} d_k
 // (prefix times suffix products), w~_m P = gamma_m f_m, f_m = P + tau^2 Q_m
-// (one fused multiply-add), so the weights need one reciprocal instead of
-// NL+2 (FP64 division is costly on B300) and r = f_0 / sum_m gamma_m f_m;
-// FP32 keeps the quotients (products of d could overflow its range).
+// (one fused multiply-add, nl_numerators), so the weights need one
+// reciprocal instead of NL+2 (FP64 division is costly on B300) and
+// r = f_0 / sum_m gamma_m f_m; FP32 keeps the quotients (products of d could
+// overflow its range).
 template <typename T, int NL>
-__device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<T>& w, T& r, T* om) {
+__device__ __forceinline__ void nl_numerators(const T* beta, T tau, const WeightsT<T>& w, T* f) {
   const T t2 = tau * tau;
   T d[NL + 1];
 #pragma unroll
   for (int m = 0; m <= NL; ++m) d[m] = (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps;
+  T pre[NL + 1], suf[NL + 1];
+  pre[1] = d[0];
+#pragma unroll
+  for (int m = 2; m <= NL; ++m) pre[m] = pre[m - 1] * d[m - 1];
+  suf[NL - 1] = d[NL];
+#pragma unroll
+  for (int m = NL - 2; m >= 0; --m) suf[m] = suf[m + 1] * d[m + 1];
+  const T P = d[0] * suf[0];
+#pragma unroll
+  for (int m = 0; m <= NL; ++m) {
+    const T q = m == 0 ? suf[0] : (m == NL ? pre[NL] : pre[m] * suf[m]);
+    f[m] = fma(t2, q, P);
+  }
+}
+
+template <typename T, int NL>
+__device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<T>& w, T& r, T* om) {
   if constexpr (sizeof(T) == 8) {
-    T pre[NL + 1], suf[NL + 1];
-    pre[1] = d[0];
-#pragma unroll
-    for (int m = 2; m <= NL; ++m) pre[m] = pre[m - 1] * d[m - 1];
-    suf[NL - 1] = d[NL];
-#pragma unroll
-    for (int m = NL - 2; m >= 0; --m) suf[m] = suf[m + 1] * d[m + 1];
-    const T P = d[0] * suf[0];
     T f[NL + 1];
-#pragma unroll
-    for (int m = 0; m <= NL; ++m) {
-      const T q = m == 0 ? suf[0] : (m == NL ? pre[NL] : pre[m] * suf[m]);
-      f[m] = fma(t2, q, P);
-    }
+    nl_numerators<T, NL>(beta, tau, w, f);
     T s = w.g[0] * f[0];
 #pragma unroll
     for (int m = 1; m <= NL; ++m) s = fma(w.g[m], f[m], s);
@@ -256,9 +262,10 @@ __device__ __forceinline__ void nl_weights(const T* beta, T tau, const WeightsT<
 #pragma unroll
     for (int m = 1; m <= NL; ++m) om[m] = (w.g[m] * f[m]) * inv;
   } else {
+    const T t2 = tau * tau;
     T e[NL + 1];
 #pragma unroll
-    for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (T(1) + div_t(t2, d[m]));
+    for (int m = 0; m <= NL; ++m) e[m] = w.g[m] * (T(1) + div_t(t2, (w.pow2 ? beta[m] * beta[m] : beta[m]) + w.eps));
     T s = e[0];
 #pragma unroll
     for (int m = 1; m <= NL; ++m) s += e[m];

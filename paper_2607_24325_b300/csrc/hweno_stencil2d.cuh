@@ -290,11 +290,10 @@ __device__ __forceinline__ T beta_typical_2d(const T* c) {
   return b;
 }
 
-// Steps 2-3 (Sec. 2.2): beta = sum (m! n! c)^2, tau = 1/4 sum |beta_0 - beta_m|,
-// the nonlinear weights; r = omega_0 / gamma_0 and om[1..4].  With DEV the
-// largest |omega_m / gamma_m - 1| is folded into *dev.
-template <typename TW, bool DEV>
-__device__ __forceinline__ void weights2(const Coef2<TW>& k, const WeightsT<TW>& w, TW& r, TW* om, TW* dev) {
+// Step 2 (Sec. 2.2): beta_0 = sum (m! n! c)^2 (or the Jiang-Shu form),
+// beta_1..4 of the linear polynomials, and tau = 1/4 sum |beta_0 - beta_m|.
+template <typename TW>
+__device__ __forceinline__ TW betas2(const Coef2<TW>& k, const WeightsT<TW>& w, TW* beta) {
   const TW* c = k.c;
   const TW b1 = k.dW * k.dW + k.dS * k.dS, b2 = k.dE * k.dE + k.dS * k.dS;
   const TW b3 = k.dE * k.dE + k.dN * k.dN, b4 = k.dW * k.dW + k.dN * k.dN;
@@ -303,8 +302,17 @@ __device__ __forceinline__ void weights2(const Coef2<TW>& k, const WeightsT<TW>&
                                 TW(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
                                 TW(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
                                 TW(576) * (c[10] * c[10] + c[14] * c[14]) + TW(16) * c[12] * c[12];
-  const TW tau = TW(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
-  const TW beta[5] = {b0, b1, b2, b3, b4};
+  beta[0] = b0; beta[1] = b1; beta[2] = b2; beta[3] = b3; beta[4] = b4;
+  return TW(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
+}
+
+// Steps 2-3 (Sec. 2.2): the indicators and the nonlinear weights;
+// r = omega_0 / gamma_0 and om[1..4].  With DEV the largest
+// |omega_m / gamma_m - 1| is folded into *dev.
+template <typename TW, bool DEV>
+__device__ __forceinline__ void weights2(const Coef2<TW>& k, const WeightsT<TW>& w, TW& r, TW* om, TW* dev) {
+  TW beta[5];
+  const TW tau = betas2<TW>(k, w, beta);
   nl_weights<TW, 4>(beta, tau, w, r, om);
   if constexpr (DEV) {
     TW d = fabs_t(r - TW(1));
@@ -315,6 +323,35 @@ __device__ __forceinline__ void weights2(const Coef2<TW>& k, const WeightsT<TW>&
     }
     *dev = d > *dev ? d : *dev;
   }
+}
+
+// FP64, Steps 2-3 and Eq. (hweno-reconstruction-2D) in one.  With the weight
+// numerators f_m (nl_numerators: w~_m P = gamma_m f_m), e_m = gamma_m f_m and
+// s = sum_m e_m: r = f_0 / s, omega_m = e_m / s, so the pair sums of omega
+// the combination takes are (e_a + e_b) / s, and sum_{m >= 1} omega_m =
+// 1 - r gamma_0 (the weights sum to 1).
+__device__ __forceinline__ void weights_combine2_f64(const Coef2<double>& k, const WeightsT<double>& w, double* cu) {
+  double beta[5], f[5];
+  const double tau = betas2<double>(k, w, beta);
+  nl_numerators<double, 4>(beta, tau, w, f);
+  const double* c = k.c;
+  const double e1 = w.g[1] * f[1], e2 = w.g[2] * f[2], e3 = w.g[3] * f[3], e4 = w.g[4] * f[4];
+  const double E12 = e1 + e2, E34 = e3 + e4;
+  const double inv = rcp_t(fma(w.g[0], f[0], E12 + E34));
+  const double r = f[0] * inv;
+  const double ws = fma(-r, w.g[0], 1.0);
+  const double gs = (w.g[1] + w.g[2]) + (w.g[3] + w.g[4]);
+  // r (c_1 - G_W dW - G_E dE) + O_W dW + O_E dE = r c_1 + (O_W - r G_W) dW + (O_E - r G_E) dE,
+  // O_W - r G_W = (e_1 + e_4 - f_0 G_W) / s
+  const double aW = (fma(-f[0], w.g[1] + w.g[4], e1 + e4)) * inv;
+  const double aE = (fma(-f[0], w.g[2] + w.g[3], e2 + e3)) * inv;
+  const double aS = (fma(-f[0], w.g[1] + w.g[2], E12)) * inv;
+  const double aN = (fma(-f[0], w.g[3] + w.g[4], E34)) * inv;
+  cu[0] = r * (c[0] - gs * k.q5) + ws * k.q5;
+  cu[1] = r * c[1] + (aW * k.dW + aE * k.dE);
+  cu[2] = r * c[2] + (aS * k.dS + aN * k.dN);
+#pragma unroll
+  for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
 }
 
 // Eq. (hweno-reconstruction-2D): cu = r (p0 - sum gamma_m p_m) + sum omega_m p_m.
@@ -350,9 +387,13 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
     for (int l = 0; l < 15; ++l) cu[l] = k.c[l];
     return;
   }
-  T r, om[5];
-  weights2<T, DEV>(k, w, r, om, dev);
-  combine2<T>(k, r, om, w, cu);
+  if constexpr (sizeof(T) == 8 && !DEV) {
+    weights_combine2_f64(k, w, cu);
+  } else {
+    T r, om[5];
+    weights2<T, DEV>(k, w, r, om, dev);
+    combine2<T>(k, r, om, w, cu);
+  }
 }
 
 // The stencil values of one field, by value (the argument of the FP64
