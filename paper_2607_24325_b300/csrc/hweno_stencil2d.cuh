@@ -21,7 +21,7 @@ constexpr int kSS = kT2 * kSP + 8;  // stash quantity stride, in cells (room for
 // at 168 registers and 10 warps at 96 (fewer warps hide less latency; 96
 // registers spill).
 template <typename T, bool W64>
-constexpr int threads2() { return 256; }
+__host__ __device__ constexpr int threads2() { return 256; }
 
 // The NC components of one cell as vector loads / stores (16-byte accesses
 // for the four Euler components; the address must be 16-byte aligned).

@@ -364,6 +364,12 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   DeferList* dl = reinterpret_cast<DeferList*>(stash + 4 * NC * kSS);  // after the stash
+  // Stages 2-3: the y pass folds w-hat into its w quantity, so the stash's
+  // fourth quantity is free during the x pass and holds, per warp, the
+  // current row's stage-update inputs (u^n, v-hat^n, w-hat^n of its cells),
+  // copied by cp.async while the row is reconstructed.
+  T* const stage_in = stash + 3 * NC * kSS;
+  static_assert((threads2<T, W64>() / 32) * 3 * NC * 32 <= NC * kSS, "update staging exceeds the stash quantity");
   __syncthreads();
   if constexpr (W64) {
     if (threadIdx.x == 0) dl->n[0] = dl->n[1] = 0;  // published by the fill's barrier
@@ -457,11 +463,30 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
           pack64<NC, CHR>(box, bidx, D, CHR && !lin, g, redo & 0xfu, redo >> 4, wx64.eps, wx64.pow2,
                           wx64.typical, a64);
       }
+      if (it == 1 && a.stage >= 2) {
+        // this row's update inputs, in flight while the row is reconstructed
+        // (a deferred row waits for its copies before it returns)
+        const int i = i0 - 1 + lane, j = j0 + r;
+        if (lane >= 1 && lane <= kT2 && i < G.nx && HW_IN(i, G.nx, 12) && HW_IN(j, G.ny, 12)) {
+          const long long p = (long long)j * G.nx + i;
+          T* sg = stage_in + warp * (3 * NC * 32) + lane;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            if (HW_IN(warp * (3 * NC * 32) + (2 * NC + k) * 32 + lane, NC * kSS, 12)) {
+              cp_async_elem(sg + k * 32, base + k * plane + p);
+              cp_async_elem(sg + (NC + k) * 32, hat + k * plane + p);
+              cp_async_elem(sg + (2 * NC + k) * 32, hat + (NC + k) * plane + p);
+            }
+          }
+        }
+      }
       T Fu[NC], Fv[NC], Fw[NC], vh[NC];
       if (!pass2d<T, EQ, CHR, W64>(box, bidx, D, wp, wp64, lin, D == 0 ? idx : idy, D == 0 ? idy : idx,
                                    D == 0 ? c.ax : c.ay, g, D == 0 ? advx_t : advy_t, Fu, Fv, Fw, vh,
-                                   redo & 0xfu, a64, &pend, &nqb))
+                                   redo & 0xfu, a64, &pend, &nqb)) {
+        if (it == 1 && a.stage >= 2) cp_async_wait_all();  // the staging slot is free again
         return false;
+      }
       // flux differences across the cell (high face, the next lane's low
       // face, minus low face): the fluxes themselves are dead from here on
       T dFu[NC], dFv[NC], dFw[NC];
@@ -482,10 +507,16 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
             sw[k] = -dFv[kk];
             sh[k] = vh[kk];
           }
+          if (a.stage >= 2) {
+            // the update's y part of w: w-hat + dt L^w_y (quantity 3 is then
+            // the x pass's staging area)
+#pragma unroll
+            for (int k = 0; k < NC; ++k) sw[k] = sh[k] + tdt * sw[k];
+          }
           stash_store<T, NC>(stash, 0, lane - 1, r, su);
           stash_store<T, NC>(stash, 1, lane - 1, r, sv);
           stash_store<T, NC>(stash, 2, lane - 1, r, sw);
-          stash_store<T, NC>(stash, 3, lane - 1, r, sh);
+          if (a.stage < 2) stash_store<T, NC>(stash, 3, lane - 1, r, sh);
         }
         return true;
       }
@@ -497,35 +528,44 @@ __device__ __forceinline__ void tile2d(const Stage2Args& a, const Grid2& G, int 
         stash_load<T, NC>(stash, 0, r, lane - 1, yu);
         stash_load<T, NC>(stash, 1, r, lane - 1, yv);
         stash_load<T, NC>(stash, 2, r, lane - 1, yw);
-        stash_load<T, NC>(stash, 3, r, lane - 1, yh);
+        if (a.stage < 2) stash_load<T, NC>(stash, 3, r, lane - 1, yh);
         if (a.stage != 0) box_load<T, NC>(box, 0, (r + 2) * kBP + lane + 1, 0, ubox);
         T nu[NC];
+        if (a.stage >= 2) {
+          // u^n, v-hat^n, w-hat^n of this cell from the staging area (each
+          // lane reads only what its own copies wrote)
+          cp_async_wait_all();
+          const T* sg = stage_in + warp * (3 * NC * 32) + lane;
+          const T cA = a.stage == 2 ? T(0.75) : T(1.0 / 3.0), cB = a.stage == 2 ? T(0.25) : T(2.0 / 3.0);
+          const T tdx = tdt * dyx;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-          const T Lu = yu[k] - dFu[k] * idx;
-          const T Lv = yv[k] - dFv[k];
-          const T Lw = yw[k] - dFw[k] * dyx;
-          const T vx = vh[k];
-          const T wyv = yh[k];
-          const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
-          const long long hv = k * plane + p, hw_ = (NC + k) * plane + p;
-          if (a.stage == 0) {
-            out[iu] = Lu; out[iv] = Lv; out[iw] = Lw;
-            hat[hv] = vx; hat[hw_] = wyv;
-          } else {
-            const T su = ubox[k] + tdt * Lu, sv = vx + tdt * Lv, sw = wyv + tdt * Lw;
-            if (a.stage == 1) {
-              out[iu] = su; out[iv] = sv; out[iw] = sw;
+          for (int k = 0; k < NC; ++k) {
+            const T un = sg[k * 32], vn = sg[(NC + k) * 32], wn = sg[(2 * NC + k) * 32];
+            const T su = ubox[k] + tdt * (yu[k] - dFu[k] * idx);
+            const T sv = vh[k] + tdt * (yv[k] - dFv[k]);
+            const T sw = yw[k] - tdx * dFw[k];  // w-hat + dt (L^w_y + L^w_x)
+            const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
+            nu[k] = cA * un + cB * su;
+            out[iu] = nu[k];
+            out[iv] = cA * vn + cB * sv;
+            out[iw] = cA * wn + cB * sw;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const T Lu = yu[k] - dFu[k] * idx;
+            const T Lv = yv[k] - dFv[k];
+            const T Lw = yw[k] - dFw[k] * dyx;
+            const T vx = vh[k];
+            const T wyv = yh[k];
+            const long long iu = k * plane + p, iv = (NC + k) * plane + p, iw = (2 * NC + k) * plane + p;
+            const long long hv = k * plane + p, hw_ = (NC + k) * plane + p;
+            if (a.stage == 0) {
+              out[iu] = Lu; out[iv] = Lv; out[iw] = Lw;
               hat[hv] = vx; hat[hw_] = wyv;
-            } else if (a.stage == 2) {
-              out[iu] = T(0.75) * base[iu] + T(0.25) * su;
-              out[iv] = T(0.75) * hat[hv] + T(0.25) * sv;
-              out[iw] = T(0.75) * hat[hw_] + T(0.25) * sw;
             } else {
-              nu[k] = base[iu] * T(1.0 / 3.0) + T(2.0 / 3.0) * su;
-              out[iv] = hat[hv] * T(1.0 / 3.0) + T(2.0 / 3.0) * sv;
-              out[iw] = hat[hw_] * T(1.0 / 3.0) + T(2.0 / 3.0) * sw;
-              out[iu] = nu[k];
+              out[iu] = ubox[k] + tdt * Lu; out[iv] = vx + tdt * Lv; out[iw] = wyv + tdt * Lw;
+              hat[hv] = vx; hat[hw_] = wyv;
             }
           }
         }
