@@ -89,6 +89,13 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
   const int lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
   const long long total = a.total;
+  // stage 3: this lane's running spectral-radius maximum over the warp's
+  // tasks of instance rinst, folded into the instance's alpha when the
+  // instance changes and after the last task (one atomic per warp and
+  // instance instead of one per task: a single-instance grid otherwise
+  // serialises hundreds of thousands of atomics on one address)
+  double rmax = 0.0;
+  int rinst = -1;
 
   for (int task = blockIdx.x * wpb + (threadIdx.x >> 5); task < a.ntasks; task += gridDim.x * wpb) {
     const int2 tk = a.tasks[task];
@@ -120,6 +127,19 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
     }
     if (lane == 0) load_cell1<T, NC, EQ>(in, total, I, lc - 1, um, vm);
     if (lane == 31) load_cell1<T, NC, EQ>(in, total, I, min(cell + 1, I.n + 1), up, vp);
+    const bool interior = lane >= 1 && lane <= kTile1 && cell < I.n && HW_IN(cell, I.n, 22) &&
+                          HW_IN(I.off + cell, total, 22);
+    // stages 2-3: the update's u^n and v-hat^n, loaded now so that their
+    // latency overlaps the reconstruction (at stage 3 base aliases out; this
+    // cell is written only by this lane, after these loads)
+    T bn[NC], hn[NC];
+    if (a.stage >= 2 && interior) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) {
+        bn[k] = base[k * total + I.off + cell];
+        hn[k] = hat[k * total + I.off + cell];
+      }
+    }
 
     T dx, idx;
     if constexpr (sizeof(T) == 4) {
@@ -163,8 +183,6 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
       Gu[k] = __shfl_down_sync(HW_FULL_MASK, Fu[k], 1);
       Gv[k] = __shfl_down_sync(HW_FULL_MASK, Fv[k], 1);
     }
-    const bool interior = lane >= 1 && lane <= kTile1 && cell < I.n && HW_IN(cell, I.n, 22) &&
-                          HW_IN(I.off + cell, total, 22);
     double rad = 0.0;
     if (interior) {
       const long long p = I.off + cell;
@@ -183,11 +201,11 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
           out[iv] = vh[k] + tdt * Lv;
           hat[k * total + p] = vh[k];
         } else if (a.stage == 2) {
-          out[iu] = T(0.75) * base[iu] + T(0.25) * (ub[k] + tdt * Lu);
-          out[iv] = T(0.75) * hat[k * total + p] + T(0.25) * (vh[k] + tdt * Lv);
+          out[iu] = T(0.75) * bn[k] + T(0.25) * (ub[k] + tdt * Lu);
+          out[iv] = T(0.75) * hn[k] + T(0.25) * (vh[k] + tdt * Lv);
         } else {
-          nu[k] = base[iu] * T(1.0 / 3.0) + T(2.0 / 3.0) * (ub[k] + tdt * Lu);
-          out[iv] = hat[k * total + p] * T(1.0 / 3.0) + T(2.0 / 3.0) * (vh[k] + tdt * Lv);
+          nu[k] = bn[k] * T(1.0 / 3.0) + T(2.0 / 3.0) * (ub[k] + tdt * Lu);
+          out[iv] = hn[k] * T(1.0 / 3.0) + T(2.0 / 3.0) * (vh[k] + tdt * Lv);
           out[iu] = nu[k];
         }
       }
@@ -198,9 +216,21 @@ __global__ void __launch_bounds__(256) k_stage1d(const Stage1Args a) {
       }
     }
     if (a.stage == 3) {
-      rad = warp_max(rad);
-      if (lane == 0) atomic_max_nonneg(&a.ctl[tk.x].amax_x, rad);
+      if (tk.x != rinst) {  // warp-uniform
+        if (rinst >= 0) {
+          const double m = warp_max(rmax);
+          if (lane == 0) atomic_max_nonneg(&a.ctl[rinst].amax_x, m);
+        }
+        rinst = tk.x;
+        rmax = 0.0;
+      }
+      // NaN bit patterns exceed every finite one, as in the atomic
+      rmax = (unsigned long long)__double_as_longlong(rad) > (unsigned long long)__double_as_longlong(rmax) ? rad : rmax;
     }
+  }
+  if (a.stage == 3 && rinst >= 0) {
+    const double m = warp_max(rmax);
+    if (lane == 0) atomic_max_nonneg(&a.ctl[rinst].amax_x, m);
   }
 }
 
