@@ -856,16 +856,19 @@ template <typename T, int EQ, bool CHR, bool W64, bool FAST, bool BATCH>
 int Launch2<T, EQ, CHR, W64, FAST, BATCH>::per_sm = 0;
 
 // The compile-time fast form exists for the characteristic-wise Euler
-// kernels (the workloads' path); every other combination runs the
-// run-time switches.
+// kernels (the workloads' path), single grids and batches; every other
+// combination runs the run-time switches.
 inline bool fast_form(const WeightParams& wp) { return wp.pow2 == 0 && wp.typical == 0; }
 
 template <typename T, int EQ, bool CHR, bool W64 = false>
 static cudaError_t go2(const Stage2Args& a, int num_sms, cudaStream_t st, const LaunchShape& sh) {
-  if (a.batched) return Launch2<T, EQ, CHR, W64, false, true>::go(a, num_sms, st, sh);
   if constexpr (EQ == HWENO_EQ_EULER && CHR) {
-    if (fast_form(a.wp)) return Launch2<T, EQ, CHR, W64, true, false>::go(a, num_sms, st, sh);
+    if (fast_form(a.wp)) {
+      if (a.batched) return Launch2<T, EQ, CHR, W64, true, true>::go(a, num_sms, st, sh);
+      return Launch2<T, EQ, CHR, W64, true, false>::go(a, num_sms, st, sh);
+    }
   }
+  if (a.batched) return Launch2<T, EQ, CHR, W64, false, true>::go(a, num_sms, st, sh);
   return Launch2<T, EQ, CHR, W64, false, false>::go(a, num_sms, st, sh);
 }
 
@@ -873,8 +876,8 @@ template <typename T, bool W64, bool BATCH>
 static cudaError_t prep2(int equation, bool chr, bool fast) {
   if (equation == HWENO_EQ_EULER) {
     if (chr)
-      return fast && !BATCH ? Launch2<T, HWENO_EQ_EULER, true, W64, true, false>::prepare()
-                            : Launch2<T, HWENO_EQ_EULER, true, W64, false, BATCH>::prepare();
+      return fast ? Launch2<T, HWENO_EQ_EULER, true, W64, true, BATCH>::prepare()
+                  : Launch2<T, HWENO_EQ_EULER, true, W64, false, BATCH>::prepare();
     return Launch2<T, HWENO_EQ_EULER, false, W64, false, BATCH>::prepare();
   }
   if (equation == HWENO_EQ_BURGERS) return Launch2<T, HWENO_EQ_BURGERS, false, W64, false, BATCH>::prepare();
