@@ -5,6 +5,8 @@
 // and the face Gauss-point evaluation.
 #pragma once
 
+#include <string.h>
+
 #include "hweno_device.cuh"
 
 namespace hw {
@@ -268,6 +270,69 @@ __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
   o.q5 = q5;
 }
 
+// Two FP32 lanes of work in one paired instruction (FADD2 / FMUL2 / FFMA2 of
+// sm_100 and later; PTX add / sub / mul / fma .rn.f32x2): the same formula
+// for two characteristic fields at once, each half rounded as the scalar
+// instruction rounds it.
+struct f2 { float2 v; };
+__device__ __forceinline__ f2 pr(float a, float b) { return f2{make_float2(a, b)}; }
+__device__ __forceinline__ f2 sp(float a) { return f2{make_float2(a, a)}; }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2{__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+  unsigned long long ra, rb, rd;
+  memcpy(&ra, &a.v, 8);
+  memcpy(&rb, &b.v, 8);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  f2 d;
+  memcpy(&d.v, &rd, 8);
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v, b.v, c.v)}; }
+
+// coef2 (FP32, centre-shifted) for two fields at once: the FP32 formula of
+// coef2 term by term, each multiply-add fused as the compiler fuses the
+// scalar form.
+__device__ __forceinline__ void coef2_x2(const float* qa, const float* qb, Coef2<float>& oa, Coef2<float>& ob) {
+  const f2 q5 = pr(qa[4], qb[4]);
+  const f2 d1 = pr(qa[0], qb[0]) - q5, d2 = pr(qa[1], qb[1]) - q5, d3 = pr(qa[2], qb[2]) - q5;
+  const f2 d4 = pr(qa[3], qb[3]) - q5, d6 = pr(qa[5], qb[5]) - q5;
+  const f2 d7 = pr(qa[6], qb[6]) - q5, d8 = pr(qa[7], qb[7]) - q5, d9 = pr(qa[8], qb[8]) - q5;
+  const f2 q10 = pr(qa[9], qb[9]), q11 = pr(qa[10], qb[10]), q12 = pr(qa[11], qb[11]);
+  const f2 q13 = pr(qa[12], qb[12]), q14 = pr(qa[13], qb[13]), q15 = pr(qa[14], qb[14]);
+  const f2 q16 = pr(qa[15], qb[15]), q17 = pr(qa[16], qb[16]);
+  const f2 s13 = d1 + d3, s79 = d7 + d9, m13 = d1 - d3, m79 = d7 - d9;
+  const f2 sc = s13 + s79, cx = m13 - m79, ax = m13 + m79, ay = s13 - s79;
+  const f2 ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
+  const f2 s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
+  const f2 s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
+  f2 c[15];
+  c[0] = fma2(fma2(sp(81.0f), m1110 + m1716, fma2(sp(-292.0f), ex + ey, sp(5.0f) * sc)), sp(1.0f / 2880.0f), q5);
+  c[1] = fma2(sp(3.0f), s1213, fma2(sp(-6.0f), s1011, fma2(sp(19.0f), dxe, sp(2.0f) * ax))) * sp(1.0f / 24.0f);
+  c[2] = fma2(sp(-6.0f), s1617, fma2(sp(3.0f), s1415, fma2(sp(19.0f), dye, sp(2.0f) * ay))) * sp(1.0f / 24.0f);
+  c[3] = fma2(sp(-18.0f), m1110, fma2(sp(62.0f), ex, sp(2.0f) * ey) - sc) * sp(1.0f / 48.0f);
+  c[4] = fma2(sp(-0.625f), m1213 + m1415, sp(-0.375f) * cx);
+  c[5] = fma2(sp(-18.0f), m1716, fma2(sp(62.0f), ey, sp(2.0f) * ex) - sc) * sp(1.0f / 48.0f);
+  c[6] = fma2(sp(-2.0f), s1213, fma2(sp(4.0f), s1011 - dxe, sp(0.0f) - ax)) * sp(0.05f);
+  c[7] = fma2(sp(-0.5f), dye, sp(-0.25f) * ay);
+  c[8] = fma2(sp(-0.5f), dxe, sp(-0.25f) * ax);
+  c[9] = fma2(sp(-2.0f), s1415, fma2(sp(4.0f), s1617 - dye, sp(0.0f) - ay)) * sp(0.05f);
+  c[10] = fma2(sp(-0.5f), ex, sp(0.25f) * m1110);
+  c[11] = fma2(sp(0.5f), m1213, sp(0.25f) * cx);
+  c[12] = fma2(sp(-0.5f), ex + ey, sp(0.25f) * sc);
+  c[13] = fma2(sp(0.5f), m1415, sp(0.25f) * cx);
+  c[14] = fma2(sp(-0.5f), ey, sp(0.25f) * m1716);
+#pragma unroll
+  for (int l = 0; l < 15; ++l) { oa.c[l] = c[l].v.x; ob.c[l] = c[l].v.y; }
+  const f2 z = sp(0.0f);
+  const f2 dW = z - d4, dS = z - d2;
+  oa.dW = dW.v.x; ob.dW = dW.v.y;
+  oa.dE = d6.v.x; ob.dE = d6.v.y;
+  oa.dS = dS.v.x; ob.dS = dS.v.y;
+  oa.dN = d8.v.x; ob.dN = d8.v.y;
+  oa.q5 = q5.v.x; ob.q5 = q5.v.y;
+}
+
 // Jiang-Shu indicator of the 2D quartic, the 2D form of Eq.
 // (smoothness-indicator-typical): the sum over 1 <= m + n <= 4 of the
 // integrals over [-1/2, 1/2]^2 of (d^{m+n} p / dxi^m deta^n)^2, as the
@@ -375,6 +440,24 @@ __device__ __forceinline__ void combine2(const Coef2<T>& k, T r, const T* om, co
   }
 #pragma unroll
   for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
+}
+
+// Steps 2-3 for one field from its coefficients: the combined polynomial cu
+// (lin: p0 itself).
+template <typename T, bool DEV = false>
+__device__ __forceinline__ void recon2_from(const Coef2<T>& k, const WeightsT<T>& w, bool lin, T* cu, T* dev = nullptr) {
+  if (lin) {
+#pragma unroll
+    for (int l = 0; l < 15; ++l) cu[l] = k.c[l];
+    return;
+  }
+  if constexpr (sizeof(T) == 8 && !DEV) {
+    weights_combine2_f64(k, w, cu);
+  } else {
+    T r, om[5];
+    weights2<T, DEV>(k, w, r, om, dev);
+    combine2<T>(k, r, om, w, cu);
+  }
 }
 
 // Steps 1-3 for one field: the combined polynomial cu (lin: p0 itself).
@@ -616,6 +699,55 @@ __device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
   o.au = A0 + A2 * T(1.0 / 12.0) + A4 * T(0.0125);
   o.an = B0 + B2 * T(1.0 / 12.0);
   o.at = A1 + T(0.25) * A3;
+}
+
+// face_points (FP32) for two fields at once and both faces of each (right:
+// xi = +1/2, left: xi = -1/2): the even and odd parts of every face
+// coefficient once, each face from their sum or difference.
+__device__ __forceinline__ void face_points_x2(const float* ca, const float* cb, FacePts<float>& ra,
+                                               FacePts<float>& rb, FacePts<float>& la, FacePts<float>& lb) {
+  f2 c[15];
+#pragma unroll
+  for (int l = 0; l < 15; ++l) c[l] = pr(ca[l], cb[l]);
+  const float s = 0.38729833462074168852f, s2 = 0.15f, s3 = s * 0.15f, s4 = 0.0225f;
+  const f2 eA0 = fma2(sp(0.0625f), c[10], fma2(sp(0.25f), c[3], c[0]));
+  const f2 oA0 = fma2(sp(0.125f), c[6], sp(0.5f) * c[1]);
+  const f2 eA1 = fma2(sp(0.25f), c[7], c[2]);
+  const f2 oA1 = fma2(sp(0.125f), c[11], sp(0.5f) * c[4]);
+  const f2 eA2 = fma2(sp(0.25f), c[12], c[5]);
+  const f2 oA2 = sp(0.5f) * c[8];
+  const f2 eB0 = fma2(sp(0.75f), c[6], c[1]);
+  const f2 oB0 = fma2(sp(0.5f), c[10], c[3]);
+  const f2 eB1 = fma2(sp(0.75f), c[11], c[4]);
+  const f2 A4 = c[14], B3 = c[13];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const bool r = side == 0;
+    const f2 A0 = r ? eA0 + oA0 : eA0 - oA0;
+    const f2 A1 = r ? eA1 + oA1 : eA1 - oA1;
+    const f2 A2 = r ? eA2 + oA2 : eA2 - oA2;
+    const f2 A3 = fma2(sp(r ? 0.5f : -0.5f), c[13], c[9]);
+    const f2 B0 = r ? eB0 + oB0 : eB0 - oB0;
+    const f2 B1 = r ? eB1 + c[7] : eB1 - c[7];
+    const f2 B2 = r ? c[8] + c[12] : c[8] - c[12];
+    const f2 ue = fma2(A4, sp(s4), fma2(A2, sp(s2), A0)), uo = fma2(A3, sp(s3), A1 * sp(s));
+    const f2 ne = fma2(B2, sp(s2), B0), no = fma2(B3, sp(s3), B1 * sp(s));
+    const f2 te = fma2(A3, sp(3.0f * s2), A1), to = fma2(A4, sp(4.0f * s3), A2 * sp(2.0f * s));
+    const f2 u0 = ue - uo, u2 = ue + uo, n0 = ne - no, n2 = ne + no, t0 = te - to, t2 = te + to;
+    const f2 au = fma2(A4, sp(0.0125f), fma2(A2, sp(1.0f / 12.0f), A0));
+    const f2 an = fma2(B2, sp(1.0f / 12.0f), B0), at = fma2(sp(0.25f), A3, A1);
+    FacePts<float>& oa = r ? ra : la;
+    FacePts<float>& ob = r ? rb : lb;
+    oa.u[0] = u0.v.x; oa.u[1] = A0.v.x; oa.u[2] = u2.v.x;
+    ob.u[0] = u0.v.y; ob.u[1] = A0.v.y; ob.u[2] = u2.v.y;
+    oa.un[0] = n0.v.x; oa.un[1] = B0.v.x; oa.un[2] = n2.v.x;
+    ob.un[0] = n0.v.y; ob.un[1] = B0.v.y; ob.un[2] = n2.v.y;
+    oa.ut[0] = t0.v.x; oa.ut[1] = A1.v.x; oa.ut[2] = t2.v.x;
+    ob.ut[0] = t0.v.y; ob.ut[1] = A1.v.y; ob.ut[2] = t2.v.y;
+    oa.au = au.v.x; ob.au = au.v.y;
+    oa.an = an.v.x; ob.an = an.v.y;
+    oa.at = at.v.x; ob.at = at.v.y;
+  }
 }
 
 }  // namespace hw

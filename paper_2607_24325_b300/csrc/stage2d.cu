@@ -256,6 +256,15 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
         *nqb = nb;
         return false;
       }
+    } else if constexpr (sizeof(T) == 4 && NC == 4) {
+      // FP32: the coefficient maps of two fields per paired instruction
+#pragma unroll
+      for (int k = 0; k < NC; k += 2) {
+        Coef2<float> ka, kb;
+        coef2_x2(q[k], q[k + 1], ka, kb);
+        recon2_from<T>(ka, w, lin, cu[k]);
+        recon2_from<T>(kb, w, lin, cu[k + 1]);
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < NC; ++k) recon2<T>(q[k], w, lin, cu[k]);
@@ -284,10 +293,18 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
   // restrictions), starts the flux sums; v-hat is the face average of
   // u(right) - u(left) (Gauss weights summing to 1).
   const T ha = T(0.5) * alpha;
+  if constexpr (sizeof(T) == 4 && NC == 4) {
+    face_points_x2(cu[0], cu[1], fr[0], fr[1], fl[0], fl[1]);
+    face_points_x2(cu[2], cu[3], fr[2], fr[3], fl[2], fl[3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      face_points<T>(cu[k], T(1), fr[k]);
+      face_points<T>(cu[k], T(-1), fl[k]);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
-    face_points<T>(cu[k], T(1), fr[k]);
-    face_points<T>(cu[k], T(-1), fl[k]);
     Fu[k] = -ha * (fl[k].au - __shfl_up_sync(HW_FULL_MASK, fr[k].au, 1));
     Fv[k] = -ha * (fl[k].an - __shfl_up_sync(HW_FULL_MASK, fr[k].an, 1));
     Fw[k] = -ha * (fl[k].at - __shfl_up_sync(HW_FULL_MASK, fr[k].at, 1));
