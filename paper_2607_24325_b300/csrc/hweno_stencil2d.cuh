@@ -292,8 +292,12 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return f2{__ffma2_rn(a.v,
 
 // coef2 (FP32, centre-shifted) for two fields at once: the FP32 formula of
 // coef2 term by term, each multiply-add fused as the compiler fuses the
-// scalar form.
-__device__ __forceinline__ void coef2_x2(const float* qa, const float* qb, Coef2<float>& oa, Coef2<float>& ob) {
+// scalar form; the coefficients and slopes stay paired.
+struct Coef2x2 {
+  f2 c[15];
+  f2 dW, dE, dS, dN, q5;
+};
+__device__ __forceinline__ void coef2_pair(const float* qa, const float* qb, Coef2x2& o) {
   const f2 q5 = pr(qa[4], qb[4]);
   const f2 d1 = pr(qa[0], qb[0]) - q5, d2 = pr(qa[1], qb[1]) - q5, d3 = pr(qa[2], qb[2]) - q5;
   const f2 d4 = pr(qa[3], qb[3]) - q5, d6 = pr(qa[5], qb[5]) - q5;
@@ -306,31 +310,41 @@ __device__ __forceinline__ void coef2_x2(const float* qa, const float* qb, Coef2
   const f2 ex = d4 + d6, ey = d2 + d8, dxe = d6 - d4, dye = d8 - d2;
   const f2 s1011 = q10 + q11, m1110 = q11 - q10, s1213 = q12 + q13, m1213 = q12 - q13;
   const f2 s1415 = q14 + q15, m1415 = q14 - q15, s1617 = q16 + q17, m1716 = q17 - q16;
-  f2 c[15];
-  c[0] = fma2(fma2(sp(81.0f), m1110 + m1716, fma2(sp(-292.0f), ex + ey, sp(5.0f) * sc)), sp(1.0f / 2880.0f), q5);
-  c[1] = fma2(sp(3.0f), s1213, fma2(sp(-6.0f), s1011, fma2(sp(19.0f), dxe, sp(2.0f) * ax))) * sp(1.0f / 24.0f);
-  c[2] = fma2(sp(-6.0f), s1617, fma2(sp(3.0f), s1415, fma2(sp(19.0f), dye, sp(2.0f) * ay))) * sp(1.0f / 24.0f);
-  c[3] = fma2(sp(-18.0f), m1110, fma2(sp(62.0f), ex, sp(2.0f) * ey) - sc) * sp(1.0f / 48.0f);
-  c[4] = fma2(sp(-0.625f), m1213 + m1415, sp(-0.375f) * cx);
-  c[5] = fma2(sp(-18.0f), m1716, fma2(sp(62.0f), ey, sp(2.0f) * ex) - sc) * sp(1.0f / 48.0f);
-  c[6] = fma2(sp(-2.0f), s1213, fma2(sp(4.0f), s1011 - dxe, sp(0.0f) - ax)) * sp(0.05f);
-  c[7] = fma2(sp(-0.5f), dye, sp(-0.25f) * ay);
-  c[8] = fma2(sp(-0.5f), dxe, sp(-0.25f) * ax);
-  c[9] = fma2(sp(-2.0f), s1415, fma2(sp(4.0f), s1617 - dye, sp(0.0f) - ay)) * sp(0.05f);
-  c[10] = fma2(sp(-0.5f), ex, sp(0.25f) * m1110);
-  c[11] = fma2(sp(0.5f), m1213, sp(0.25f) * cx);
-  c[12] = fma2(sp(-0.5f), ex + ey, sp(0.25f) * sc);
-  c[13] = fma2(sp(0.5f), m1415, sp(0.25f) * cx);
-  c[14] = fma2(sp(-0.5f), ey, sp(0.25f) * m1716);
-#pragma unroll
-  for (int l = 0; l < 15; ++l) { oa.c[l] = c[l].v.x; ob.c[l] = c[l].v.y; }
+  o.c[0] = fma2(fma2(sp(81.0f), m1110 + m1716, fma2(sp(-292.0f), ex + ey, sp(5.0f) * sc)), sp(1.0f / 2880.0f), q5);
+  o.c[1] = fma2(sp(3.0f), s1213, fma2(sp(-6.0f), s1011, fma2(sp(19.0f), dxe, sp(2.0f) * ax))) * sp(1.0f / 24.0f);
+  o.c[2] = fma2(sp(-6.0f), s1617, fma2(sp(3.0f), s1415, fma2(sp(19.0f), dye, sp(2.0f) * ay))) * sp(1.0f / 24.0f);
+  o.c[3] = fma2(sp(-18.0f), m1110, fma2(sp(62.0f), ex, sp(2.0f) * ey) - sc) * sp(1.0f / 48.0f);
+  o.c[4] = fma2(sp(-0.625f), m1213 + m1415, sp(-0.375f) * cx);
+  o.c[5] = fma2(sp(-18.0f), m1716, fma2(sp(62.0f), ey, sp(2.0f) * ex) - sc) * sp(1.0f / 48.0f);
+  o.c[6] = fma2(sp(-2.0f), s1213, fma2(sp(4.0f), s1011 - dxe, sp(0.0f) - ax)) * sp(0.05f);
+  o.c[7] = fma2(sp(-0.5f), dye, sp(-0.25f) * ay);
+  o.c[8] = fma2(sp(-0.5f), dxe, sp(-0.25f) * ax);
+  o.c[9] = fma2(sp(-2.0f), s1415, fma2(sp(4.0f), s1617 - dye, sp(0.0f) - ay)) * sp(0.05f);
+  o.c[10] = fma2(sp(-0.5f), ex, sp(0.25f) * m1110);
+  o.c[11] = fma2(sp(0.5f), m1213, sp(0.25f) * cx);
+  o.c[12] = fma2(sp(-0.5f), ex + ey, sp(0.25f) * sc);
+  o.c[13] = fma2(sp(0.5f), m1415, sp(0.25f) * cx);
+  o.c[14] = fma2(sp(-0.5f), ey, sp(0.25f) * m1716);
   const f2 z = sp(0.0f);
-  const f2 dW = z - d4, dS = z - d2;
-  oa.dW = dW.v.x; ob.dW = dW.v.y;
-  oa.dE = d6.v.x; ob.dE = d6.v.y;
-  oa.dS = dS.v.x; ob.dS = dS.v.y;
-  oa.dN = d8.v.x; ob.dN = d8.v.y;
-  oa.q5 = q5.v.x; ob.q5 = q5.v.y;
+  o.dW = z - d4;
+  o.dE = d6;
+  o.dS = z - d2;
+  o.dN = d8;
+  o.q5 = q5;
+}
+__device__ __forceinline__ void unpack2(const Coef2x2& k, Coef2<float>& a, Coef2<float>& b) {
+#pragma unroll
+  for (int l = 0; l < 15; ++l) { a.c[l] = k.c[l].v.x; b.c[l] = k.c[l].v.y; }
+  a.dW = k.dW.v.x; b.dW = k.dW.v.y;
+  a.dE = k.dE.v.x; b.dE = k.dE.v.y;
+  a.dS = k.dS.v.x; b.dS = k.dS.v.y;
+  a.dN = k.dN.v.x; b.dN = k.dN.v.y;
+  a.q5 = k.q5.v.x; b.q5 = k.q5.v.y;
+}
+__device__ __forceinline__ void coef2_x2(const float* qa, const float* qb, Coef2<float>& oa, Coef2<float>& ob) {
+  Coef2x2 k;
+  coef2_pair(qa, qb, k);
+  unpack2(k, oa, ob);
 }
 
 // Jiang-Shu indicator of the 2D quartic, the 2D form of Eq.
@@ -477,6 +491,77 @@ __device__ __forceinline__ void recon2(const T* q, const WeightsT<T>& w, bool li
     weights2<T, DEV>(k, w, r, om, dev);
     combine2<T>(k, r, om, w, cu);
   }
+}
+
+// |x| of both halves (the sign bits cleared on the integer ALU).
+__device__ __forceinline__ f2 abs2(f2 x) {
+  return f2{make_float2(__uint_as_float(__float_as_uint(x.v.x) & 0x7fffffffu),
+                        __uint_as_float(__float_as_uint(x.v.y) & 0x7fffffffu))};
+}
+
+// FP32, Steps 1-3 for two fields at once (recon2 term by term, paired): the
+// coefficient maps, the moment indicator and the weights of Sec. 2.2 with
+// the FP32 quotients, and the combination of Eq. (hweno-reconstruction-2D).
+// The Jiang-Shu form takes the scalar path.
+__device__ __forceinline__ void recon2_x2(const float* qa, const float* qb, const WeightsT<float>& w, bool lin,
+                                          float* cua, float* cub) {
+  Coef2x2 k;
+  coef2_pair(qa, qb, k);
+  const f2* c = k.c;
+  if (lin) {
+#pragma unroll
+    for (int l = 0; l < 15; ++l) { cua[l] = c[l].v.x; cub[l] = c[l].v.y; }
+    return;
+  }
+  if (w.typical) {
+    Coef2<float> ka, kb;
+    unpack2(k, ka, kb);
+    recon2_from<float>(ka, w, false, cua);
+    recon2_from<float>(kb, w, false, cub);
+    return;
+  }
+  // Step 2: beta_0 = sum (m! n! c)^2, beta_1..4 of the linear polynomials
+  const f2 dW2 = k.dW * k.dW, dE2 = k.dE * k.dE, dS2 = k.dS * k.dS, dN2 = k.dN * k.dN;
+  f2 beta[5];
+  beta[1] = dW2 + dS2;
+  beta[2] = dE2 + dS2;
+  beta[3] = dE2 + dN2;
+  beta[4] = dW2 + dN2;
+  const f2 g4 = fma2(c[8], c[8], fma2(c[7], c[7], fma2(c[5], c[5], c[3] * c[3])));
+  const f2 g36 = fma2(c[13], c[13], fma2(c[11], c[11], fma2(c[9], c[9], c[6] * c[6])));
+  const f2 g576 = fma2(c[14], c[14], c[10] * c[10]);
+  f2 b0 = fma2(c[4], c[4], fma2(c[2], c[2], c[1] * c[1]));
+  b0 = fma2(sp(16.0f) * c[12], c[12], fma2(sp(576.0f), g576, fma2(sp(36.0f), g36, fma2(sp(4.0f), g4, b0))));
+  beta[0] = b0;
+  const f2 tau = sp(0.25f) * ((abs2(b0 - beta[1]) + abs2(b0 - beta[2])) + (abs2(b0 - beta[3]) + abs2(b0 - beta[4])));
+  // Step 3: w~_m = gamma_m (1 + tau^2 / (beta_m^p + eps)), omega = w~ / sum w~
+  const f2 t2 = tau * tau;
+  f2 e[5];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const f2 d = w.pow2 ? fma2(beta[m], beta[m], sp(w.eps)) : beta[m] + sp(w.eps);
+    const f2 a = t2 * pr(rcp_approx(d.v.x), rcp_approx(d.v.y));
+    e[m] = fma2(sp(w.g[m]), a, sp(w.g[m]));
+  }
+  const f2 sum = ((e[0] + e[1]) + (e[2] + e[3])) + e[4];
+  const f2 inv = pr(rcp_approx(sum.v.x), rcp_approx(sum.v.y));
+  const f2 r = (e[0] * inv) * sp(w.inv_g0);
+  f2 om[5];
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) om[m] = e[m] * inv;
+  // Eq. (hweno-reconstruction-2D): cu = r (p0 - sum gamma_m p_m) + sum omega_m p_m
+  const float gs = (w.g[1] + w.g[2]) + (w.g[3] + w.g[4]);
+  const f2 ws = (om[1] + om[2]) + (om[3] + om[4]);
+  f2 cu[15];
+  cu[0] = fma2(ws, k.q5, r * fma2(sp(-gs), k.q5, c[0]));
+  cu[1] = fma2(om[2] + om[3], k.dE, (om[1] + om[4]) * k.dW) +
+          r * (c[1] - fma2(sp(w.g[2] + w.g[3]), k.dE, sp(w.g[1] + w.g[4]) * k.dW));
+  cu[2] = fma2(om[3] + om[4], k.dN, (om[1] + om[2]) * k.dS) +
+          r * (c[2] - fma2(sp(w.g[3] + w.g[4]), k.dN, sp(w.g[1] + w.g[2]) * k.dS));
+#pragma unroll
+  for (int l = 3; l < 15; ++l) cu[l] = r * c[l];
+#pragma unroll
+  for (int l = 0; l < 15; ++l) { cua[l] = cu[l].v.x; cub[l] = cu[l].v.y; }
 }
 
 // The stencil values of one field, by value (the argument of the FP64

@@ -257,14 +257,9 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
         return false;
       }
     } else if constexpr (sizeof(T) == 4 && NC == 4) {
-      // FP32: the coefficient maps of two fields per paired instruction
+      // FP32: Steps 1-3 of two fields per paired instruction
 #pragma unroll
-      for (int k = 0; k < NC; k += 2) {
-        Coef2<float> ka, kb;
-        coef2_x2(q[k], q[k + 1], ka, kb);
-        recon2_from<T>(ka, w, lin, cu[k]);
-        recon2_from<T>(kb, w, lin, cu[k + 1]);
-      }
+      for (int k = 0; k < NC; k += 2) recon2_x2(q[k], q[k + 1], w, lin, cu[k], cu[k + 1]);
     } else {
 #pragma unroll
       for (int k = 0; k < NC; ++k) recon2<T>(q[k], w, lin, cu[k]);
