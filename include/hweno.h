@@ -250,14 +250,17 @@ hweno_status hweno_peak_fma(int precision, double* flops_per_second);
 hweno_status hweno_selftest_convert(const float* f_in, double* wide_out, const double* d_in, float* narrow_out,
                                     int n);
 
-/* Self-check of the FP64 reciprocal the FP64 kernels use (Newton-Raphson from
- * an FP32 seed, two steps, for 1/rho in the fluxes and eigenvectors and the
- * normalisation of the nonlinear weights).  Not part of the paper's method:
- * a diagnostic that exposes that routine.  For i < n (device pointers,
- * caller-owned): y_out[i] = the library's 1 / x_in[i], to be within one unit
- * in the last place of the correctly rounded quotient.  Launches on the
- * legacy default stream and synchronises the device.  HWENO_ERR_ARG for
- * n < 0 or a null pointer with n > 0. */
+/* Self-check of the FP64 reciprocal the FP64 kernels use (two Newton-Raphson
+ * steps from the hardware's approximate FP64 reciprocal, for 1/rho in the
+ * fluxes and eigenvectors, 1/c, and the normalisation of the nonlinear
+ * weights).  Not part of the paper's method: a diagnostic that exposes that
+ * routine.  For i < n (device pointers, caller-owned): y_out[i] = the
+ * library's 1 / x_in[i], to be within one unit in the last place of the
+ * correctly rounded quotient wherever x_in[i] and its reciprocal are normal
+ * numbers; zeros, infinities and NaN give the IEEE results, subnormal
+ * arguments and results are flushed (+-inf, +-0).  Launches on the legacy
+ * default stream and synchronises the device.  HWENO_ERR_ARG for n < 0 or a
+ * null pointer with n > 0. */
 hweno_status hweno_selftest_rcp64(const double* x_in, double* y_out, int n);
 
 /* Autotuner: time the candidate launch shapes of the stage kernel on the
