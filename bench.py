@@ -71,16 +71,17 @@ ALGO_FLOPS = {
 ALGO_SOURCE = ("algorithmic: the method's formulas in plain evaluation per cell and stage "
                "(oracle/flops.py, equal to the instrumented oracle's count)")
 # What the 2D Euler characteristic-wise stage kernel executes per interior
-# cell-stage (ncu FP op counters, 2 per FMA, at 1536^2, the ring-lane
+# cell-stage (ncu FP op counters, 2 per FMA and 2 per paired FP32 lane, at
+# 1536^2, the ring-lane
 # redundancy removed; profiles/stage2d_euler_char_counters_1536.md): the
 # kernel evaluates the same formulas with fewer operations (centre-shifted
 # maps, face restrictions shared by the Gauss points, symmetric Gauss pairs).
-EXEC_FLOPS = {("euler2d_char", "f64"): 5087.0, ("euler2d_char", "f32"): 4831.0}
+EXEC_FLOPS = {("euler2d_char", "f64"): 5087.0, ("euler2d_char", "f32"): 4801.0}
 MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.2  # executed, early-time 1536^2 state; data dependent
 # DRAM bytes per cell of the 2D Euler stage kernel, mean of the three stage
 # launches at 2048^2 (state larger than L2), scaled to the grid by cells;
 # None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 268.7, "fp32": 130.0, "fp32_ind64": 135.0}
+TRAFFIC_PER_CELL = {"fp64": 268.7, "fp32": 130.8, "fp32_ind64": 135.4}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 2048^2, scaled to the grid by cells"
 # Stored fields F and limited-derivative fields D per cell: stage 1 reads F
 # and writes F + D, stages 2-3 read 2F and write F -> (8F + D)/3 words per
