@@ -29,7 +29,8 @@ def _floats(rng):
 
 
 def _doubles(rng):
-    f = np.ldexp(rng.uniform(1.0, 2.0, 50_000), rng.integers(-140, 130, 50_000)).astype(np.float32)
+    with np.errstate(over="ignore"):   # exponents past the FP32 range become infinities, then dropped
+        f = np.ldexp(rng.uniform(1.0, 2.0, 50_000), rng.integers(-140, 130, 50_000)).astype(np.float32)
     f = f[np.isfinite(f) & (f != 0)]
     fd = f.astype(np.float64)
     half = np.spacing(np.abs(f)).astype(np.float64) / 2.0
@@ -58,7 +59,8 @@ def test_conversions_match_ieee():
     wide, narrow = hw.hweno_selftest_convert(torch.from_numpy(f).cuda(), torch.from_numpy(d).cuda())
     w = wide.cpu().numpy()
     nr = narrow.cpu().numpy()
-    ok_w = _same(w, f.astype(np.float64))
+    with np.errstate(invalid="ignore"):   # NaN payloads among the random bit patterns
+        ok_w = _same(w, f.astype(np.float64))
     with np.errstate(over="ignore"):
         ref_n = d.astype(np.float32)
     ok_n = _same(nr, ref_n)
