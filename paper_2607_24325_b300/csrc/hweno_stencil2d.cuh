@@ -202,6 +202,7 @@ template <typename TC>
 struct Coef2 {
   TC c[15];
   TC dW, dE, dS, dN, q5;
+  TC S;  // with SC: the largest |d_k| and |moment| (the FP32 screen's scale)
 };
 
 // The coefficients are evaluated on the centre-shifted averages
@@ -210,8 +211,9 @@ struct Coef2 {
 // cancels exactly, and the rounding of each coefficient scales with the
 // local variation instead of with |q5| (in FP32 the difference of two nearby
 // averages is exact).  With C0 = false, c_0 is not formed (the smoothness
-// indicator does not use it).
-template <typename TC, typename TQ, bool C0 = true>
+// indicator does not use it); with SC, S is formed too, so that the stencil
+// values are dead once the coefficients exist.
+template <typename TC, typename TQ, bool C0 = true, bool SC = false>
 __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
   const TC q5 = to_tc<TC>(qin[4]);
   const TC d1 = to_tc<TC>(qin[0]) - q5, d2 = to_tc<TC>(qin[1]) - q5, d3 = to_tc<TC>(qin[2]) - q5;
@@ -268,6 +270,13 @@ __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
   o.dS = -d2;
   o.dN = d8;
   o.q5 = q5;
+  if constexpr (SC) {
+    const TC dd[16] = {d1, d2, d3, d4, d6, d7, d8, d9, q10, q11, q12, q13, q14, q15, q16, q17};
+    TC S = TC(0);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) S = fmax(S, fabs_t(dd[t]));
+    o.S = S;
+  }
 }
 
 // Two FP32 lanes of work in one paired instruction (FADD2 / FMUL2 / FFMA2 of
@@ -660,13 +669,12 @@ static __device__ __noinline__ Weights5 indicator64(const Stencil17 st, double e
 // where every a_m = tau^2 / (beta_m^p + eps) is provably below 2^-24, so
 // that 1 + a_m is 1 in FP32 and a_m = 0 gives the FP64 evaluation's result
 // bit for bit.
-__device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, const WeightsT<double>& w,
+__device__ __forceinline__ bool screen2(const Coef2<float>& k, const WeightsT<double>& w,
                                         const WeightsT<float>& wf) {
   // verification build (libhweno_noscreen.so, which sets screen_off on the
   // host and compiles the same device code): every lane takes the FP64
   // indicator, to show that the screen never changes an output bit
   if (wf.screen_off) return false;
-  const float q5f = q[4];
   // FP32 screen: a sound upper bound on every a_m = tau^2 / (beta_m^p + eps)
   // from the FP32 coefficients k.  Each c~_l combines the stencil differences
   // and moments (largest magnitude S) and errs by at most ~30 u S in FP32
@@ -685,12 +693,8 @@ __device__ __forceinline__ bool screen2(const float* q, const Coef2<float>& k, c
   // (any sound bound keeps this; a looser one only skips less often).
   bool quiet;
   {
-    float S = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 9; ++s)
-      if (s != 4) S = fmaxf(S, fabsf(q[s] - q5f));
-#pragma unroll
-    for (int s = 9; s < 17; ++s) S = fmaxf(S, fabsf(q[s]));
+    // S: the largest stencil difference or moment (k.S, formed with the coefficients)
+    const float S = k.S;
     const float* c = k.c;
     const float E = S * 0x1p-16f;
     float bs[5], Ds[5];

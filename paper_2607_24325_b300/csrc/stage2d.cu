@@ -228,7 +228,7 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
 #pragma unroll
       for (int k = 0; k < NC; ++k) {
         Coef2<float> kc;
-        coef2<float, float>(q[k], kc);
+        coef2<float, float, true, true>(q[k], kc);
         if (lin) {
 #pragma unroll
           for (int l = 0; l < 15; ++l) cu[k][l] = kc.c[l];
@@ -238,7 +238,7 @@ __device__ __forceinline__ bool pass2d(const T* __restrict__ box, int bidx, int 
 #pragma unroll
         for (int m = 1; m < 5; ++m) om[m] = om0[m];
         if (redo == 0u) {
-          const bool quiet = screen2(q[k], kc, w64, w);
+          const bool quiet = screen2(kc, w64, w);
           if (!__all_sync(HW_FULL_MASK, quiet)) {
             pe |= 1u << k;
             nb |= quiet ? 0u : 1u << k;
