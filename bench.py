@@ -81,7 +81,7 @@ MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.2  # executed, early-time 1536^2 state; dat
 # DRAM bytes per cell of the 2D Euler stage kernel, mean of the three stage
 # launches at 2048^2 (state larger than L2), scaled to the grid by cells;
 # None once the kernel has changed since the capture.
-TRAFFIC_PER_CELL = {"fp64": 268.7, "fp32": 130.8, "fp32_ind64": 135.4}
+TRAFFIC_PER_CELL = {"fp64": 268.7, "fp32": 130.8, "fp32_ind64": 135.0}
 TRAFFIC_NOTE = "mean DRAM bytes of the three stage launches at 2048^2, scaled to the grid by cells"
 # Stored fields F and limited-derivative fields D per cell: stage 1 reads F
 # and writes F + D, stages 2-3 read 2F and write F -> (8F + D)/3 words per
