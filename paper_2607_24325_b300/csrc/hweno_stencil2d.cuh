@@ -198,6 +198,10 @@ __device__ __forceinline__ T load_ghost2(const T* __restrict__ in, long long pla
 // xi^4, xi^3 eta, xi^2 eta^2, xi eta^3, eta^4}) from q1..q17, and the slopes
 // of the linear p1..p4 = q5 + sx xi + sy eta on S1 {W,S}, S2 {E,S}, S3 {E,N},
 // S4 {W,N}.  TC is the arithmetic type, TQ the type of the inputs.
+// The scale of coefficient l as the FP64 coefficient map forms it (the FP32
+// map forms the coefficients themselves).
+__host__ __device__ constexpr double sc2(int l) { return l == 6 || l == 9 ? 20.0 : (l >= 7 ? 4.0 : 1.0); }
+
 template <typename TC>
 struct Coef2 {
   TC c[15];
@@ -256,15 +260,31 @@ __device__ __forceinline__ void coef2(const TQ* qin, Coef2<TC>& o) {
     c[5] = (TC(2) * ex + TC(62) * ey - sc - TC(18) * m1716) * TC(1.0 / 48.0);
   }
   c[4] = TC(-0.375) * cx - TC(0.625) * (m1213 + m1415);
-  c[6] = (TC(4) * (s1011 - dxe) - ax - TC(2) * s1213) * TC(0.05);
-  c[7] = TC(-0.25) * ay - TC(0.5) * dye;
-  c[8] = TC(-0.25) * ax - TC(0.5) * dxe;
-  c[9] = (TC(4) * (s1617 - dye) - ay - TC(2) * s1415) * TC(0.05);
-  c[10] = TC(0.25) * m1110 - TC(0.5) * ex;
-  c[11] = TC(0.25) * cx + TC(0.5) * m1213;
-  c[12] = TC(0.25) * sc - TC(0.5) * (ex + ey);
-  c[13] = TC(0.25) * cx + TC(0.5) * m1415;
-  c[14] = TC(0.25) * m1716 - TC(0.5) * ey;
+  if constexpr (sizeof(TC) == 8) {
+    // FP64: c_6 and c_9 scaled by 20 and c_7, c_8, c_10..c_14 by 4 (sc2): each
+    // is then one fused multiply-add of the shared sums, and the scales are
+    // folded into the constants of their readers (betas2, face_points); the
+    // combination and the back-projection are linear per coefficient
+    c[6] = TC(4) * (s1011 - dxe) - ax - TC(2) * s1213;
+    c[7] = -ay - TC(2) * dye;
+    c[8] = -ax - TC(2) * dxe;
+    c[9] = TC(4) * (s1617 - dye) - ay - TC(2) * s1415;
+    c[10] = m1110 - TC(2) * ex;
+    c[11] = cx + TC(2) * m1213;
+    c[12] = sc - TC(2) * (ex + ey);
+    c[13] = cx + TC(2) * m1415;
+    c[14] = m1716 - TC(2) * ey;
+  } else {
+    c[6] = (TC(4) * (s1011 - dxe) - ax - TC(2) * s1213) * TC(0.05);
+    c[7] = TC(-0.25) * ay - TC(0.5) * dye;
+    c[8] = TC(-0.25) * ax - TC(0.5) * dxe;
+    c[9] = (TC(4) * (s1617 - dye) - ay - TC(2) * s1415) * TC(0.05);
+    c[10] = TC(0.25) * m1110 - TC(0.5) * ex;
+    c[11] = TC(0.25) * cx + TC(0.5) * m1213;
+    c[12] = TC(0.25) * sc - TC(0.5) * (ex + ey);
+    c[13] = TC(0.25) * cx + TC(0.5) * m1415;
+    c[14] = TC(0.25) * m1716 - TC(0.5) * ey;
+  }
   o.dW = -d4;
   o.dE = d6;
   o.dS = -d2;
@@ -385,11 +405,27 @@ __device__ __forceinline__ TW betas2(const Coef2<TW>& k, const WeightsT<TW>& w, 
   const TW* c = k.c;
   const TW b1 = k.dW * k.dW + k.dS * k.dS, b2 = k.dE * k.dE + k.dS * k.dS;
   const TW b3 = k.dE * k.dE + k.dN * k.dN, b4 = k.dW * k.dW + k.dN * k.dN;
-  const TW b0 = w.typical ? beta_typical_2d(c)
-                          : c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
-                                TW(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
-                                TW(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
-                                TW(576) * (c[10] * c[10] + c[14] * c[14]) + TW(16) * c[12] * c[12];
+  TW b0;
+  if constexpr (sizeof(TW) == 8) {
+    // the FP64 coefficients carry the scales sc2: the weights (m! n!)^2 / sc2^2
+    if (w.typical) {
+      TW cu[15];
+#pragma unroll
+      for (int l = 0; l < 15; ++l) cu[l] = c[l] * TW(1.0 / sc2(l));
+      b0 = beta_typical_2d(cu);
+    } else {
+      b0 = c[1] * c[1] + c[2] * c[2] + c[4] * c[4] + TW(4) * (c[3] * c[3] + c[5] * c[5]) +
+           TW(0.25) * (c[7] * c[7] + c[8] * c[8]) + TW(0.09) * (c[6] * c[6] + c[9] * c[9]) +
+           TW(2.25) * (c[11] * c[11] + c[13] * c[13]) + TW(36) * (c[10] * c[10] + c[14] * c[14]) +
+           c[12] * c[12];
+    }
+  } else {
+    b0 = w.typical ? beta_typical_2d(c)
+                   : c[1] * c[1] + c[2] * c[2] + c[4] * c[4] +
+                         TW(4) * (c[3] * c[3] + c[5] * c[5] + c[7] * c[7] + c[8] * c[8]) +
+                         TW(36) * (c[6] * c[6] + c[9] * c[9] + c[11] * c[11] + c[13] * c[13]) +
+                         TW(576) * (c[10] * c[10] + c[14] * c[14]) + TW(16) * c[12] * c[12];
+  }
   beta[0] = b0; beta[1] = b1; beta[2] = b2; beta[3] = b3; beta[4] = b4;
   return TW(0.25) * ((fabs_t(b0 - b1) + fabs_t(b0 - b2)) + (fabs_t(b0 - b3) + fabs_t(b0 - b4)));
 }
@@ -769,6 +805,31 @@ struct FacePts { T u[3], un[3], ut[3], au, an, at; };
 
 template <typename T>
 __device__ __forceinline__ void face_points(const T* c, T sgn, FacePts<T>& o) {
+  if constexpr (sizeof(T) == 8) {
+    // FP64: the coefficients carry the scales sc2 (c_6, c_9 x 20; c_7, c_8,
+    // c_10..c_14 x 4); A3 = 20 A3, A4 = 4 A4, B2 = 4 B2 and B3 = 4 B3 below,
+    // their scales folded into the constants that read them
+    const double s = 0.38729833462074168852, s2 = 0.15, s3 = s * 0.15, s4 = 0.0225;
+    const double A0 = (c[0] + 0.25 * c[3] + 0.015625 * c[10]) + sgn * (0.5 * c[1] + 0.00625 * c[6]);
+    const double A1 = (c[2] + 0.0625 * c[7]) + sgn * (0.5 * c[4] + 0.03125 * c[11]);
+    const double A2 = (c[5] + 0.0625 * c[12]) + sgn * (0.125 * c[8]);
+    const double A3 = c[9] + sgn * (2.5 * c[13]);
+    const double A4 = c[14];
+    const double B0 = (c[1] + 0.0375 * c[6]) + sgn * (c[3] + 0.125 * c[10]);
+    const double B1 = (c[4] + 0.1875 * c[11]) + sgn * (0.25 * c[7]);
+    const double B2 = c[8] + sgn * c[12];
+    const double B3 = c[13];
+    const double ue = A0 + A2 * s2 + A4 * (s4 / 4), uo = A1 * s + A3 * (s3 / 20);
+    const double ne = B0 + B2 * (s2 / 4), no = B1 * s + B3 * (s3 / 4);
+    const double te = A1 + A3 * (3 * s2 / 20), to = A2 * (2 * s) + A4 * s3;
+    o.u[0] = ue - uo; o.u[1] = A0; o.u[2] = ue + uo;
+    o.un[0] = ne - no; o.un[1] = B0; o.un[2] = ne + no;
+    o.ut[0] = te - to; o.ut[1] = A1; o.ut[2] = te + to;
+    o.au = A0 + A2 * (1.0 / 12.0) + A4 * (0.0125 / 4);
+    o.an = B0 + B2 * (1.0 / 48.0);
+    o.at = A1 + A3 * (0.25 / 20);
+    return;
+  }
   const T s = T(0.38729833462074168852), s2 = T(0.15), s3 = s * T(0.15), s4 = T(0.0225);
   const T A0 = (c[0] + T(0.25) * c[3] + T(0.0625) * c[10]) + sgn * (T(0.5) * c[1] + T(0.125) * c[6]);
   const T A1 = (c[2] + T(0.25) * c[7]) + sgn * (T(0.5) * c[4] + T(0.125) * c[11]);
