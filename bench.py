@@ -76,7 +76,7 @@ ALGO_SOURCE = ("algorithmic: the method's formulas in plain evaluation per cell 
 # redundancy removed; profiles/stage2d_euler_char_counters_1536.md): the
 # kernel evaluates the same formulas with fewer operations (centre-shifted
 # maps, face restrictions shared by the Gauss points, symmetric Gauss pairs).
-EXEC_FLOPS = {("euler2d_char", "f64"): 5087.0, ("euler2d_char", "f32"): 4801.0}
+EXEC_FLOPS = {("euler2d_char", "f64"): 4999.0, ("euler2d_char", "f32"): 4801.0}
 MIXED_FP64_FLOPS_PER_CELL_STAGE = 10.2  # executed, early-time 1536^2 state; data dependent
 # DRAM bytes per cell of the 2D Euler stage kernel, mean of the three stage
 # launches at 2048^2 (state larger than L2), scaled to the grid by cells;
