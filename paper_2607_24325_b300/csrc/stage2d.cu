@@ -3,18 +3,22 @@
 // A CTA (8 warps) owns a 30 x 30 tile of interior cells.  It stages the
 // 34 x 34 box (tile + 2-cell halo) of every field in shared memory, resolving
 // ghost cells with the boundary map on the way in, then runs
-//   x pass: warp per row, lane l = cell i0-1+l.  Each lane reconstructs its
-//           cell (characteristic-wise with the x eigenvectors of its own
-//           average for Euler), evaluates u, u_x, u_y at the 3 Gauss points
-//           of both x faces, takes its left neighbour's right-face values by
-//           shuffle and forms the Lax-Friedrichs fluxes of its LEFT face
-//           (each interface once); the right-face flux comes from lane+1.
-//           The x part of L and v-hat go to a shared-memory stash.
-//   y pass: the same code on the transposed box (warp per column, lanes
-//           along y).  Transposing swaps the roles of x and y, of v-bar and
-//           w-bar, of the two momentum components and of the stencils S2 and
-//           S4, so the y physics is the x physics in the transposed frame.
-//           It adds the y part of L and applies the RK stage.
+//   y pass: warp per tile column, lanes along y, on the transposed box.
+//           Transposing swaps the roles of x and y, of v-bar and w-bar, of
+//           the two momentum components and of the stencils S2 and S4, so the
+//           y physics is the x physics in the transposed frame and both
+//           passes run one copy of the code.  Each lane reconstructs its cell
+//           (characteristic-wise with the eigenvectors of its own average for
+//           Euler), evaluates u and its two derivatives at the 3 Gauss points
+//           of both faces, takes its left neighbour's right-face values by
+//           shuffle and forms the Lax-Friedrichs fluxes of its LOW face (each
+//           interface once; the high-face flux comes from lane+1).  The y part
+//           of L and w-hat go to a shared-memory stash.
+//   x pass: warp per tile row, lane l = cell i0-1+l, the same code on the
+//           box; it adds the x part of L and applies the RK stage, with
+//           coalesced global stores along x (stages 2-3 take u^n, v-hat^n and
+//           w-hat^n of the row from shared memory, copied there by cp.async
+//           while the row is reconstructed).
 // Interface values, fluxes and L never go through HBM.
 #include <cuda_runtime.h>
 
